@@ -1,0 +1,94 @@
+"""Pins for the oracle's range finder, Apx-EVD, LAI products and leverage scores."""
+
+import numpy as np
+
+from oracle import symnmf as O
+from synth import gaussian_sketch, gmm_points, kernel_matrix_numpy, median_pair_distance, planted_dense, uniform_factor
+
+
+def _lowrank_sym(n, r, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, r))
+    d = rng.uniform(0.5, 2.0, size=r) * rng.choice([-1, 1], size=r)
+    return (B * d) @ B.T
+
+
+def test_exact_range_capture_when_rank_at_most_l():
+    X = _lowrank_sym(300, 12, seed=0)
+    U, lam = O.apx_evd(X, gaussian_sketch(300, 20, seed=1), q=2)
+    err = np.linalg.norm(X - U @ np.diag(lam) @ U.T) / np.linalg.norm(X)
+    assert err <= 1e-10
+    np.testing.assert_allclose(U.T @ U, np.eye(20), atol=1e-10)
+
+
+def test_planted_rank_k_captured():
+    X, H0, _ = planted_dense(n=400, k=8, sigma=0.0, seed=2)
+    U, lam = O.apx_evd(X, gaussian_sketch(400, 26, seed=3), q=1)
+    assert np.linalg.norm(X - U @ np.diag(lam) @ U.T) / np.linalg.norm(X) <= 1e-10
+
+
+def test_lai_product_is_projected_operator():
+    # U Lambda U^T = P X P with P = Q Q^T (Alg. Apx-EVD)
+    pts, _ = gmm_points(300, 5, 4, seed=0)
+    X = kernel_matrix_numpy(pts, median_pair_distance(pts, seed=0))
+    Om = gaussian_sketch(300, 15, seed=4)
+    Q = O.rrf(X, Om, q=2)
+    U, lam = O.apx_evd(X, Om, q=2)
+    P = Q @ Q.T
+    F = np.random.default_rng(0).random((300, 6))
+    np.testing.assert_allclose(O.lai_product(U, lam, F), P @ X @ P @ F, rtol=1e-9, atol=1e-10)
+
+
+def test_qb_residual_identity():
+    # ||Q B - X||^2 = ||X||^2 - ||B||^2 for B = Q^T X (Ada-RRF appendix)
+    X = _lowrank_sym(200, 30, seed=5) + 0.01 * np.eye(200)
+    Q = O.rrf(X, gaussian_sketch(200, 12, seed=6), q=1)
+    B = Q.T @ X
+    lhs = np.linalg.norm(Q @ B - X) ** 2
+    rhs = np.linalg.norm(X) ** 2 - np.linalg.norm(B) ** 2
+    assert abs(lhs - rhs) <= 1e-9 * np.linalg.norm(X) ** 2
+
+
+def test_evd_projection_bound():
+    # ||X - P X P|| <= 2 ||X - P X|| (Section 'Approximation Errors for LAI-NMF')
+    pts, _ = gmm_points(250, 6, 5, seed=3)
+    X = kernel_matrix_numpy(pts, median_pair_distance(pts, seed=3))
+    Q = O.rrf(X, gaussian_sketch(250, 10, seed=7), q=0)
+    P = Q @ Q.T
+    assert np.linalg.norm(X - P @ X @ P) <= 2 * np.linalg.norm(X - P @ X) + 1e-12
+
+
+def test_lai_iterates_equal_full_iterates_when_range_captured():
+    X, _, _ = planted_dense(n=300, k=6, sigma=0.0, seed=4)
+    alpha = O.default_alpha(X)
+    U, lam = O.apx_evd(X, gaussian_sketch(300, 16, seed=8), q=2)
+    H0 = uniform_factor(300, 6, seed=9) * O.init_scale(X, 6)
+    W1, H1, o1 = O.hals_symnmf(X, H0, alpha, 100)
+    W2, H2, o2 = O.lai_symnmf(U, lam, H0, alpha, 100)
+    np.testing.assert_allclose(H2, H1, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(o2, o1, rtol=1e-8)
+
+
+def test_leverage_scores_match_householder_and_svd():
+    rng = np.random.default_rng(10)
+    F = rng.random((500, 9))
+    lev, full = O.leverage_scores(F)
+    assert full
+    Qh, _ = np.linalg.qr(F)
+    np.testing.assert_allclose(lev, (Qh ** 2).sum(1), rtol=1e-10, atol=1e-14)
+    Us, _, _ = np.linalg.svd(F, full_matrices=False)
+    np.testing.assert_allclose(lev, (Us ** 2).sum(1), rtol=1e-10, atol=1e-14)
+    assert abs(lev.sum() - 9) < 1e-10
+    assert lev.min() >= 0 and lev.max() <= 1 + 1e-12
+
+
+def test_leverage_scores_rank_deficient():
+    rng = np.random.default_rng(11)
+    F = rng.random((200, 6))
+    F[:, 3] = 0.0
+    lev, full = O.leverage_scores(F)
+    assert not full
+    assert abs(lev.sum() - 5) < 1e-9
+    Us, s, _ = np.linalg.svd(F, full_matrices=False)
+    r = (s > 1e-10 * s[0]).sum()
+    np.testing.assert_allclose(lev, (Us[:, :r] ** 2).sum(1), rtol=1e-9, atol=1e-13)
