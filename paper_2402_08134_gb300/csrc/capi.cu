@@ -1,0 +1,836 @@
+// C ABI of the SymNMF library: the solver handle and the driver of the hot
+// path.  Every numerical step runs in this library's kernels; this file only
+// sequences them on the handle's stream, records sweep bodies as CUDA graphs,
+// and maps errors to status codes.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/symnmf.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "handle.h"
+
+namespace symnmf {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches += n; }
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cached = v;
+  }
+  return cached;
+}
+
+symnmf_status to_status(cudaError_t e) {
+  switch (e) {
+    case cudaSuccess: return SYMNMF_OK;
+    case cudaErrorMemoryAllocation: return SYMNMF_ENOMEM;
+    case cudaErrorInvalidValue: return SYMNMF_EINVAL;
+    default: return SYMNMF_ECUDA;
+  }
+}
+
+}  // namespace symnmf
+
+using namespace symnmf;
+
+// ------------------------------------------------------------------ helpers
+
+static symnmf_status fail(symnmf_t h, symnmf_status s, const std::string& msg) {
+  if (h) h->msg = msg;
+  return s;
+}
+
+static symnmf_status cuda_fail(symnmf_t h, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SYMNMF_OK;
+  cudaGetLastError();
+  return fail(h, to_status(e), std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TRY(call)                                        \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
+  } while (0)
+
+#define TRYS(call)                       \
+  do {                                   \
+    symnmf_status _s = (call);           \
+    if (_s != SYMNMF_OK) return _s;      \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(symnmf_t h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) h->allocs.push_back((void*)*p);
+  return e;
+}
+
+// Read and clear the device error word (synchronises the stream).
+static symnmf_status check_device_error(symnmf_t h) {
+  TRY(cudaStreamSynchronize(h->st));
+  unsigned e = 0;
+  TRY(cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e) TRY(cudaMemset(h->err, 0, sizeof(unsigned)));
+  if (e & ERR_TIMEOUT) return fail(h, SYMNMF_ETIMEOUT, "a bounded device wait ran out");
+  if (e & ERR_NOTSPD) return fail(h, SYMNMF_ENOTSPD, "Gram matrix is not positive definite");
+  if (e & ERR_NAN) return fail(h, SYMNMF_ENAN, "non-finite value in a factor");
+  if (e & ERR_BPP_ITERS) h->msg = "BPP reached its iteration cap on some rows (result kept)";
+  return SYMNMF_OK;
+}
+
+static bool is_dense(int fmt) { return fmt >= SYMNMF_X_DENSE_F64 && fmt <= SYMNMF_X_DENSE_FP8; }
+
+// Workspace for a dense / sparse product of width N.
+static symnmf_status ensure_gemm_ws(symnmf_t h, int N) {
+  size_t need = 0;
+  const int fmt = h->p.fmt;
+  if (fmt == SYMNMF_X_DENSE_F32 || fmt == SYMNMF_X_DENSE_F64 || h->p.x_hi)
+    need = xf_simt_ws_floats(h->n, N);
+  if (fmt == SYMNMF_X_DENSE_BF16 || fmt == SYMNMF_X_DENSE_FP8) {
+    const int BN = tc_block_n(N);
+    const size_t t = xf_tc_ws_floats(h->n, BN);
+    if (t > need) need = t;
+    const size_t pack = (size_t)BN * h->ldp * (fmt == SYMNMF_X_DENSE_BF16 ? 2 : 1);
+    if (pack > h->fpack_bytes) {
+      if (h->capturing) return fail(h, SYMNMF_ESTATE, "allocation during graph capture");
+      void* p;
+      TRY(dalloc(h, (char**)&p, pack));
+      h->fpack = p;
+      h->fpack_bytes = pack;
+    }
+    if (!h->colscale) TRY(dalloc(h, &h->colscale, 256));
+  }
+  if (need > h->gemm_ws_floats) {
+    if (h->capturing) return fail(h, SYMNMF_ESTATE, "allocation during graph capture");
+    TRY(dalloc(h, &h->gemm_ws, need));
+    h->gemm_ws_floats = need;
+  }
+  return SYMNMF_OK;
+}
+
+// Y (n x N, ld ldy) = X F for the operator `src` (SRC_X or SRC_XHI).
+symnmf_status product(symnmf_t h, int src, const float* F, int N, int ldf, float* Y, int ldy) {
+  TRYS(ensure_gemm_ws(h, N));
+  if (src == SYMNMF_SRC_XHI) {
+    TRY(xf_simt(SYMNMF_X_DENSE_F32, h->p.x_hi, h->ldx_hi, h->n, F, ldf, N, Y, ldy, h->gemm_ws,
+                h->gemm_ws_floats, h->st));
+    return SYMNMF_OK;
+  }
+  const int fmt = h->p.fmt;
+  switch (fmt) {
+    case SYMNMF_X_DENSE_F64:
+    case SYMNMF_X_DENSE_F32:
+      if (h->o.gemm == SYMNMF_GEMM_TC) return fail(h, SYMNMF_EUNSUPPORTED, "tcgen05 path needs BF16/FP8 X");
+      TRY(xf_simt(fmt, h->p.x, h->ldx, h->n, F, ldf, N, Y, ldy, h->gemm_ws, h->gemm_ws_floats, h->st));
+      return SYMNMF_OK;
+    case SYMNMF_X_DENSE_BF16:
+    case SYMNMF_X_DENSE_FP8: {
+      if (h->o.gemm == SYMNMF_GEMM_SIMT) return fail(h, SYMNMF_EUNSUPPORTED, "SIMT path needs F32/F64 X");
+      const int BN = tc_block_n(N);
+      if (fmt == SYMNMF_X_DENSE_BF16)
+        TRY(pack_ft_bf16(F, h->n, ldf, N, BN, h->fpack, h->ldp, h->st));
+      else
+        TRY(pack_ft_fp8(F, h->n, ldf, N, BN, h->fpack, h->ldp, h->colscale, h->st));
+      TRY(xf_tc(fmt, h->p.x, h->ldx, h->p.row_scale, h->n, h->fpack, h->ldp, h->colscale, N, Y, ldy,
+                h->gemm_ws, h->gemm_ws_floats, h->err, h->st));
+      return SYMNMF_OK;
+    }
+    case SYMNMF_X_CSR_F32:
+      TRY(csr_xf(h->p.row_ptr, h->p.col, (const float*)h->p.x, h->n, F, ldf, N, Y, ldy, h->st));
+      return SYMNMF_OK;
+  }
+  return fail(h, SYMNMF_EINVAL, "unknown X format");
+}
+
+static const double* normx_for(symnmf_t h, int src) {
+  if (src == SYMNMF_SRC_LAI) return h->scal + S_LAI_NORM2;
+  if (src == SYMNMF_SRC_XHI) return h->scal + S_XHI_NORM2;
+  return h->scal + S_NORM2;
+}
+
+// One half sweep: update F_upd (side 0: W, side 1: H) from the fixed factor.
+static symnmf_status half_sweep(symnmf_t h, int side, int src, int rule) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  float* Fu = side ? h->H : h->W;
+  const float* Ff = side ? h->W : h->H;
+  const int gfix = side ? 1 : 0;  // Gd[0] = H^T H, Gd[1] = W^T W
+  const int gupd = side ? 0 : 1;
+  const float* Y = nullptr;
+  const float* U = nullptr;
+  const float* M = nullptr;
+  if (src == SYMNMF_SRC_LAI) {
+    // M = Lambda (U^T F) (l x k), Y_r = U_r M fused into the update
+    TRY(xcross(h->U, h->l, h->l, Ff, k, k, n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf,
+               h->ws, h->counters + 0, h->st));
+    U = h->U;
+    M = h->Mf;
+  } else {
+    TRYS(product(h, src, Ff, k, k, h->Y, k));
+    Y = h->Y;
+  }
+  if (rule == SYMNMF_RULE_HALS)
+    TRY(hals_update(Fu, Ff, n, k, 1, h->Gf[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
+                    h->counters + 1, h->err, h->st));
+  else
+    TRY(bpp_rows(Fu, Ff, n, k, h->Gd[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
+                 h->counters + 1, h->err, h->st));
+  TRY(xcross(Fu, k, k, Fu, k, k, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[gupd], h->Gf[gupd],
+             h->ws, h->counters + 2, h->st));
+  if (side == 1)
+    TRY(objective(normx_for(h, src), h->Gd[1], h->Gd[0], k, h->scal + S_PART, h->scal + S_ALPHA,
+                  h->obj_ring, h->obj_cnt, OBJ_RING, h->st));
+  return SYMNMF_OK;
+}
+
+static symnmf_status sweep_body(symnmf_t h, int src, int rule) {
+  TRYS(half_sweep(h, 0, src, rule));
+  TRYS(half_sweep(h, 1, src, rule));
+  return SYMNMF_OK;
+}
+
+static symnmf_status refresh_grams(symnmf_t h) {
+  const int k = h->k;
+  TRY(xcross(h->H, k, k, h->H, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[0], h->Gf[0],
+             h->ws, h->counters + 2, h->st));
+  TRY(xcross(h->W, k, k, h->W, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[1], h->Gf[1],
+             h->ws, h->counters + 2, h->st));
+  return SYMNMF_OK;
+}
+
+// ---------------------------------------------------------------- create
+
+extern "C" symnmf_status symnmf_create(const symnmf_problem* prob, const symnmf_options* opt, void* stream,
+                                       symnmf_t* out) {
+  if (!out || !prob) return SYMNMF_EINVAL;
+  *out = nullptr;
+  const symnmf_problem& p = *prob;
+  if (p.n < 1 || p.k < 1 || p.k > 64 || !p.x) return SYMNMF_EINVAL;
+  if (p.fmt < SYMNMF_X_DENSE_F64 || p.fmt > SYMNMF_X_CSR_F32) return SYMNMF_EINVAL;
+  if (p.fmt == SYMNMF_X_CSR_F32 && (!p.row_ptr || !p.col || p.nnz < 0)) return SYMNMF_EINVAL;
+  if (p.fmt == SYMNMF_X_DENSE_FP8 && !p.row_scale) return SYMNMF_EINVAL;
+  const int64_t ldx = p.ldx > 0 ? p.ldx : p.n;
+  if (is_dense(p.fmt) && ldx < p.n) return SYMNMF_EINVAL;
+  if (p.fmt == SYMNMF_X_DENSE_BF16 && ((ldx % 8) || ((uintptr_t)p.x & 15))) return SYMNMF_EINVAL;
+  if (p.fmt == SYMNMF_X_DENSE_FP8 && ((ldx % 16) || ((uintptr_t)p.x & 15))) return SYMNMF_EINVAL;
+  const int64_t ldx_hi = p.ldx_hi > 0 ? p.ldx_hi : p.n;
+  if (p.x_hi && ldx_hi < p.n) return SYMNMF_EINVAL;
+
+  symnmf_t h = new symnmf_ctx();
+  h->p = p;
+  if (opt) h->o = *opt;
+  if (h->o.max_width <= 0) h->o.max_width = 2 * p.k + 10;
+  if (h->o.max_width > 96) h->o.max_width = 96;
+  h->st = (cudaStream_t)stream;
+  h->n = p.n;
+  h->k = p.k;
+  h->ldx = ldx;
+  h->ldx_hi = ldx_hi;
+  h->ldp = (p.n + 15) / 16 * 16;
+  const int64_t n = p.n;
+  const int k = p.k;
+  auto bail = [&](cudaError_t e) {
+    symnmf_status s = to_status(e);
+    symnmf_destroy(h);
+    return s;
+  };
+#define CALLOC(ptr, cnt)                          \
+  do {                                            \
+    cudaError_t _e = dalloc(h, &(ptr), (cnt));    \
+    if (_e != cudaSuccess) return bail(_e);       \
+  } while (0)
+  CALLOC(h->H, (size_t)n * k);
+  CALLOC(h->W, (size_t)n * k);
+  CALLOC(h->Y, (size_t)n * k);
+  for (int i = 0; i < 2; ++i) {
+    CALLOC(h->Gd[i], (size_t)k * k);
+    CALLOC(h->Gf[i], (size_t)k * k);
+  }
+  CALLOC(h->Gs_d, (size_t)k * k);
+  CALLOC(h->Gs_f, (size_t)k * k);
+  CALLOC(h->scal, (size_t)S_COUNT);
+  CALLOC(h->obj_ring, (size_t)OBJ_RING);
+  CALLOC(h->obj_cnt, 4);
+  h->ws_doubles = xcross_ws_doubles(96, 96);
+  if (h->ws_doubles < 3 * 4096) h->ws_doubles = 3 * 4096;
+  CALLOC(h->ws, h->ws_doubles);
+  CALLOC(h->counters, 16);
+  CALLOC(h->err, 4);
+  CALLOC(h->Rinv_d, (size_t)k * k);
+  CALLOC(h->Rinv_f, (size_t)k * k);
+#undef CALLOC
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->counters, 0, 16 * sizeof(unsigned), h->st)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(h->err, 0, 4 * sizeof(unsigned), h->st)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(h->scal, 0, S_COUNT * sizeof(double), h->st)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(h->H, 0, (size_t)n * k * 4, h->st)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(h->W, 0, (size_t)n * k * 4, h->st)) != cudaSuccess) return bail(e);
+  // ||X||^2, max(X), mean(X)
+  if ((e = xstats(p.fmt, p.x, ldx, p.row_scale, n, p.row_ptr, p.nnz, h->scal + S_MAX, h->ws,
+                  h->counters + 3, h->st)) != cudaSuccess)
+    return bail(e);
+  if (p.x_hi &&
+      (e = xstats(SYMNMF_X_DENSE_F32, p.x_hi, ldx_hi, nullptr, n, nullptr, 0, h->scal + S_XHI_MAX, h->ws,
+                  h->counters + 3, h->st)) != cudaSuccess)
+    return bail(e);
+  if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return bail(e);
+  double st3[3];
+  if ((e = cudaMemcpy(st3, h->scal + S_MAX, 3 * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bail(e);
+  double mx = st3[0];
+  if (p.fmt == SYMNMF_X_CSR_F32 && p.nnz < n * n) mx = fmax(mx, 0.0);  // implicit zeros
+  h->alpha = p.alpha > 0 ? p.alpha : mx;
+  h->normX2 = st3[2];
+  if (!(h->alpha > 0.0)) {
+    symnmf_destroy(h);
+    return SYMNMF_EINVAL;  // alpha must be positive (X has no positive entry)
+  }
+  double host_scal[S_COUNT];
+  if ((e = cudaMemcpy(host_scal, h->scal, sizeof(host_scal), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bail(e);
+  host_scal[S_ALPHA] = h->alpha;
+  host_scal[S_NORM2] = st3[2];
+  host_scal[S_MEAN] = st3[1] / ((double)n * (double)n);
+  if (!p.x_hi) host_scal[S_XHI_NORM2] = host_scal[S_NORM2];
+  if ((e = cudaMemcpy(h->scal, host_scal, sizeof(host_scal), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e);
+  symnmf_status s = ensure_gemm_ws(h, k);
+  if (s != SYMNMF_OK) {
+    symnmf_destroy(h);
+    return s;
+  }
+  *out = h;
+  return SYMNMF_OK;
+}
+
+extern "C" void symnmf_destroy(symnmf_t h) {
+  if (!h) return;
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+extern "C" const char* symnmf_last_error(symnmf_t h) { return h ? h->msg.c_str() : "null handle"; }
+
+extern "C" symnmf_status symnmf_info(symnmf_t h, double* alpha, double* normX2) {
+  if (!h) return SYMNMF_EINVAL;
+  if (alpha) *alpha = h->alpha;
+  if (normX2) *normX2 = h->normX2;
+  return SYMNMF_OK;
+}
+
+extern "C" uint64_t symnmf_launch_count(void) { return g_launches.load(); }
+
+// --------------------------------------------------------------- factors
+
+extern "C" symnmf_status symnmf_set_factors(symnmf_t h, const float* H0, const float* W0) {
+  if (!h || !H0) return SYMNMF_EINVAL;
+  const size_t bytes = (size_t)h->n * h->k * sizeof(float);
+  TRY(cudaMemcpyAsync(h->H, H0, bytes, cudaMemcpyDeviceToDevice, h->st));
+  TRY(cudaMemcpyAsync(h->W, W0 ? W0 : H0, bytes, cudaMemcpyDeviceToDevice, h->st));
+  TRY(cudaMemsetAsync(h->counters + 8, 0, sizeof(unsigned), h->st));
+  TRY(check_factor(h->H, (int64_t)h->n * h->k, h->counters + 8, h->st));
+  TRY(check_factor(h->W, (int64_t)h->n * h->k, h->counters + 8, h->st));
+  unsigned flags = 0;
+  TRY(cudaMemcpyAsync(&flags, h->counters + 8, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  TRY(cudaStreamSynchronize(h->st));
+  TRY(cudaMemsetAsync(h->counters + 8, 0, sizeof(unsigned), h->st));
+  if (flags) return fail(h, SYMNMF_EINVAL, "starting factors must be finite and nonnegative");
+  TRYS(refresh_grams(h));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_init_random(symnmf_t h, int scaled) {
+  if (!h) return SYMNMF_EINVAL;
+  TRY(philox_uniform(h->H, h->n, h->k, h->p.seed, scaled ? h->scal + S_MEAN : nullptr,
+                     2.0 / sqrt((double)h->k), h->st));
+  TRY(cudaMemcpyAsync(h->W, h->H, (size_t)h->n * h->k * 4, cudaMemcpyDeviceToDevice, h->st));
+  TRYS(refresh_grams(h));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_get_factors(symnmf_t h, float* H_out, float* W_out) {
+  if (!h) return SYMNMF_EINVAL;
+  const size_t bytes = (size_t)h->n * h->k * sizeof(float);
+  if (H_out) TRY(cudaMemcpyAsync(H_out, h->H, bytes, cudaMemcpyDeviceToDevice, h->st));
+  if (W_out) TRY(cudaMemcpyAsync(W_out, h->W, bytes, cudaMemcpyDeviceToDevice, h->st));
+  return SYMNMF_OK;
+}
+
+// ------------------------------------------------------------------- LAI
+
+static symnmf_status ensure_lai(symnmf_t h, int l) {
+  if (h->lai_cap >= l) return SYMNMF_OK;
+  const int L = h->o.max_width;
+  const size_t nl = (size_t)h->n * L;
+  TRY(dalloc(h, &h->Om, nl));
+  TRY(dalloc(h, &h->Qa, nl));
+  TRY(dalloc(h, &h->Qb, nl));
+  TRY(dalloc(h, &h->U, nl));
+  TRY(dalloc(h, &h->Mf, (size_t)L * 64));
+  TRY(dalloc(h, &h->Sm_d, (size_t)L * L));
+  TRY(dalloc(h, &h->V_d, (size_t)L * L));
+  TRY(dalloc(h, &h->lam, (size_t)L));
+  TRY(dalloc(h, &h->ev, (size_t)L));
+  TRY(dalloc(h, &h->Sm_f, (size_t)L * L));
+  TRY(dalloc(h, &h->Rl_f, (size_t)L * L));
+  h->lai_cap = L;
+  TRYS(ensure_gemm_ws(h, L));
+  return SYMNMF_OK;
+}
+
+// Rank-safe orthonormalisation of S (n x l) in place, T scratch (n x l):
+// shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
+// SIAM J. Sci. Comput. 2020).  Pass 1 factors S^T S + 1e-6 max_i (S^T S)_ii I,
+// which is positive definite whatever the rank of S; passes 2 and 3 are
+// plain CholeskyQR.  Gram matrices are accumulated in FP64 and factored in
+// FP64; pivots below 1e-10 of the largest diagonal entry are dropped (a zero
+// column of Q), so a rank-deficient sketch keeps exactly its numerical range.
+static symnmf_status orth(symnmf_t h, float* S, float* T, int l) {
+  const int64_t n = h->n;
+  float* src = S;
+  float* dst = T;
+  for (int pass = 0; pass < 3; ++pass) {
+    TRY(xcross(src, l, l, src, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
+               h->counters + 0, h->st));
+    TRY(chol_inverse(h->Sm_d, l, pass == 0 ? -1e-6 : 0.0, pass == 0 ? 1e-12 : 1e-10, nullptr, h->Rl_f, h->err,
+                     h->st));
+    TRY(apply_small(src, l, l, h->Rl_f, l, n, dst, l, h->st));
+    float* t = src;
+    src = dst;
+    dst = t;
+  }
+  // three passes: the result is in T; copy back into S
+  TRY(cudaMemcpyAsync(S, src, (size_t)n * l * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega) {
+  if (!h) return SYMNMF_EINVAL;
+  if (l < h->k || l > h->o.max_width || q < 0) return fail(h, SYMNMF_EINVAL, "need k <= l <= max_width, q >= 0");
+  if (h->p.fmt == SYMNMF_X_CSR_F32 && l > 128) return SYMNMF_EINVAL;
+  TRYS(ensure_lai(h, l));
+  const int64_t n = h->n;
+  if (omega)
+    TRY(cudaMemcpyAsync(h->Om, omega, (size_t)n * l * 4, cudaMemcpyDeviceToDevice, h->st));
+  else
+    TRY(philox_gaussian(h->Om, n, l, h->p.seed, h->st));
+  float* A = h->Qa;
+  float* B = h->Qb;
+  TRYS(product(h, SYMNMF_SRC_X, h->Om, l, l, A, l));  // Y = X Omega
+  TRYS(orth(h, A, B, l));
+  for (int j = 0; j < q; ++j) {
+    TRYS(product(h, SYMNMF_SRC_X, A, l, l, B, l));  // X^T Q (= X Q)
+    TRYS(orth(h, B, A, l));
+    TRYS(product(h, SYMNMF_SRC_X, B, l, l, A, l));  // X Q
+    TRYS(orth(h, A, B, l));
+  }
+  // Apx-EVD: T = Q^T X Q, T = V Lambda V^T, U = Q V
+  TRYS(product(h, SYMNMF_SRC_X, A, l, l, B, l));
+  TRY(xcross(A, l, l, B, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
+             h->counters + 0, h->st));
+  TRY(jacobi_evd(h->Sm_d, l, h->V_d, h->lam, h->st));
+  TRY(to_float_scaled(h->V_d, l, l, nullptr, h->Sm_f, h->st));
+  TRY(apply_small(A, l, l, h->Sm_f, l, n, h->U, l, h->st));
+  TRY(sumsq(h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  h->l = l;
+  h->lai_ready = true;
+  h->lai_version++;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_get_lai(symnmf_t h, float* U_out, double* lam_out, int* l_out) {
+  if (!h) return SYMNMF_EINVAL;
+  if (!h->lai_ready) return fail(h, SYMNMF_ESTATE, "no sketch yet");
+  if (U_out) TRY(cudaMemcpyAsync(U_out, h->U, (size_t)h->n * h->l * 4, cudaMemcpyDeviceToDevice, h->st));
+  if (lam_out) {
+    TRY(cudaMemcpyAsync(lam_out, h->lam, (size_t)h->l * 8, cudaMemcpyDeviceToHost, h->st));
+    TRY(cudaStreamSynchronize(h->st));
+  }
+  if (l_out) *l_out = h->l;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_sketch_features(symnmf_t h, float* out) {
+  if (!h || !out) return SYMNMF_EINVAL;
+  if (!h->lai_ready) return fail(h, SYMNMF_ESTATE, "no sketch yet");
+  // X Omega of the fixed Omega, row-normalised (the warm-start network input)
+  TRYS(product(h, SYMNMF_SRC_X, h->Om, h->l, h->l, h->Qb, h->l));
+  TRY(normalize_rows(h->Qb, h->n, h->l, out, h->st));
+  return SYMNMF_OK;
+}
+
+// ---------------------------------------------------------------- sweeps
+
+static symnmf_status validate_sweep(symnmf_t h, int src, int rule) {
+  if (src == SYMNMF_SRC_LAI && !h->lai_ready) return fail(h, SYMNMF_ESTATE, "LAI sweep before lai_sketch");
+  if (src == SYMNMF_SRC_XHI && !h->p.x_hi) return fail(h, SYMNMF_ESTATE, "no float32 copy of X given");
+  if (src < 0 || src > 2) return fail(h, SYMNMF_EINVAL, "bad source");
+  if (rule == SYMNMF_RULE_BPP && h->k > 16) return fail(h, SYMNMF_EUNSUPPORTED, "BPP rule needs k <= 16");
+  if (rule != SYMNMF_RULE_HALS && rule != SYMNMF_RULE_BPP) return fail(h, SYMNMF_EINVAL, "bad rule");
+  return SYMNMF_OK;
+}
+
+static symnmf_status get_graph(symnmf_t h, int src, int rule, symnmf_ctx::Graph** out) {
+  for (auto& g : h->graphs)
+    if (g.exec && g.src == src && g.rule == rule && g.lai_version == h->lai_version) {
+      *out = &g;
+      return SYMNMF_OK;
+    }
+  // one eager sweep first sizes every workspace, so capture allocates nothing
+  symnmf_ctx::Graph* slot = nullptr;
+  for (auto& g : h->graphs)
+    if (!g.exec) {
+      slot = &g;
+      break;
+    }
+  if (!slot) {
+    slot = &h->graphs[0];
+    cudaGraphExecDestroy(slot->exec);
+    slot->exec = nullptr;
+  }
+  // record on a private stream (the caller's stream may be the legacy NULL
+  // stream, which cannot be captured); the graph is launched on the caller's
+  if (!h->cap_st) TRY(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  cudaStream_t saved = h->st;
+  h->st = h->cap_st;
+  cudaError_t eb = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+  if (eb != cudaSuccess) {
+    h->st = saved;
+    return cuda_fail(h, eb, "cudaStreamBeginCapture");
+  }
+  h->capturing = true;
+  const uint64_t before = g_launches.load();
+  symnmf_status s = sweep_body(h, src, rule);
+  h->capturing = false;
+  cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+  h->st = saved;
+  if (s != SYMNMF_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return s;
+  }
+  TRY(e);
+  cudaError_t ei = cudaGraphInstantiate(&slot->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  TRY(ei);
+  slot->nkernels = g_launches.load() - before;
+  g_launches -= slot->nkernels;  // captured, not launched
+  slot->src = src;
+  slot->rule = rule;
+  slot->lai_version = h->lai_version;
+  *out = slot;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, double* obj_host) {
+  if (!h || nsweeps < 0) return SYMNMF_EINVAL;
+  TRYS(validate_sweep(h, source, rule));
+  int done = 0;
+  bool warmed = false;
+  while (done < nsweeps) {
+    const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
+    TRY(cudaMemsetAsync(h->obj_cnt, 0, sizeof(int), h->st));
+    int t = 0;
+    if (h->o.use_graph) {
+      if (!warmed) {
+        // first sweep eagerly: workspaces get sized outside capture
+        TRYS(sweep_body(h, source, rule));
+        ++t;
+        warmed = true;
+      }
+      symnmf_ctx::Graph* g = nullptr;
+      if (t < chunk) TRYS(get_graph(h, source, rule, &g));
+      for (; t < chunk; ++t) {
+        TRY(cudaGraphLaunch(g->exec, h->st));
+        count_launches(g->nkernels);
+      }
+    } else {
+      for (; t < chunk; ++t) TRYS(sweep_body(h, source, rule));
+    }
+    if (obj_host) {
+      TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->st));
+      TRYS(check_device_error(h));
+    }
+    done += chunk;
+  }
+  return SYMNMF_OK;
+}
+
+// ---------------------------------------------------------------- LvS
+
+static symnmf_status ensure_sampler(symnmf_t h, int s) {
+  const int cap = (int)((h->n > s ? h->n : s));
+  if (h->sb.cap >= cap) return SYMNMF_OK;
+  SampleBufs& b = h->sb;
+  const int nblk = sampler_blocks(h->n);
+  TRY(dalloc(h, &b.lev, (size_t)h->n));
+  TRY(dalloc(h, &b.cdf, (size_t)h->n));
+  TRY(dalloc(h, &b.idx, (size_t)cap));
+  TRY(dalloc(h, &b.wt, (size_t)cap));
+  TRY(dalloc(h, &b.counts, 4));
+  TRY(dalloc(h, &b.sums, 4));
+  TRY(dalloc(h, &b.total, 1));
+  TRY(dalloc(h, &b.blk_cnt, (size_t)nblk));
+  TRY(dalloc(h, &b.blk_q, (size_t)nblk));
+  TRY(dalloc(h, &b.blk_theta, (size_t)nblk));
+  TRY(dalloc(h, &b.blk_mass, (size_t)nblk));
+  b.nblk_cap = nblk;
+  b.cap = cap;
+  return SYMNMF_OK;
+}
+
+// Leverage scores of the fixed factor of `side` into sb.lev.
+static symnmf_status leverage_dev(symnmf_t h, int side) {
+  const float* F = side ? h->W : h->H;
+  const int k = h->k;
+  TRY(xcross(F, k, k, F, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gs_d, nullptr, h->ws,
+             h->counters + 4, h->st));
+  TRY(chol_inverse(h->Gs_d, k, 0.0, 0.0, h->Rinv_d, h->Rinv_f, h->err, h->st));
+  TRY(leverage_rows(F, h->n, k, h->Rinv_f, h->sb.lev, h->st));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_leverage(symnmf_t h, int side, double* lev_out) {
+  if (!h || (side != 0 && side != 1)) return SYMNMF_EINVAL;
+  TRYS(ensure_sampler(h, 0));
+  TRYS(leverage_dev(h, side));
+  if (lev_out) TRY(cudaMemcpyAsync(lev_out, h->sb.lev, (size_t)h->n * 8, cudaMemcpyDeviceToDevice, h->st));
+  return check_device_error(h);
+}
+
+static symnmf_status sample_dev(symnmf_t h, int side, int iter, double tau, int s) {
+  TRY(hybrid_sample(h->sb, h->n, h->k, tau, s, h->p.seed, (uint32_t)iter, (uint32_t)side, h->st));
+  h->sample_side = side;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_lvs_sample(symnmf_t h, int side, int iter, double tau, int s,
+                                           const double* lev_in, int32_t* idx_out, float* wt_out, int cap,
+                                           int* s_det, int* s_tot, double* theta) {
+  if (!h || (side != 0 && side != 1) || s < 0 || !(tau >= 0.0)) return SYMNMF_EINVAL;
+  TRYS(ensure_sampler(h, s));
+  if (lev_in)
+    TRY(cudaMemcpyAsync(h->sb.lev, lev_in, (size_t)h->n * 8, cudaMemcpyHostToDevice, h->st));
+  else
+    TRYS(leverage_dev(h, side));
+  TRYS(sample_dev(h, side, iter, tau, s));
+  int counts[4];
+  double sums[4];
+  TRY(cudaMemcpyAsync(counts, h->sb.counts, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  TRY(cudaMemcpyAsync(sums, h->sb.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  TRYS(check_device_error(h));
+  const int tot = counts[2];
+  const int m = cap < tot ? cap : tot;
+  if (idx_out && m > 0) TRY(cudaMemcpy(idx_out, h->sb.idx, (size_t)m * 4, cudaMemcpyDeviceToHost));
+  if (wt_out && m > 0) TRY(cudaMemcpy(wt_out, h->sb.wt, (size_t)m * 4, cudaMemcpyDeviceToHost));
+  if (s_det) *s_det = counts[0];
+  if (s_tot) *s_tot = tot;
+  if (theta) *theta = sums[0];
+  return SYMNMF_OK;
+}
+
+static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule) {
+  const int k = h->k;
+  const int64_t n = h->n;
+  const float* Ff = side ? h->W : h->H;
+  float* Fu = side ? h->H : h->W;
+  // Y = X S^T S F (the HALS / BPP kernels add alpha F themselves)
+  TRY(cudaMemsetAsync(h->Y, 0, (size_t)n * k * 4, h->st));
+  if (h->p.fmt == SYMNMF_X_CSR_F32)
+    TRY(csr_sampled_xf(h->p.row_ptr, h->p.col, (const float*)h->p.x, h->sb.idx, h->sb.wt, h->sb.counts + 2,
+                       Ff, k, h->Y, h->st));
+  else
+    TRY(dense_sampled_xf(h->p.fmt, h->p.x, h->ldx, n, h->sb.idx, h->sb.wt, h->sb.counts + 2, h->sb.cap, Ff,
+                         k, h->Y, h->st));
+  // G = F^T S^T S F
+  TRY(xcross(Ff, k, k, Ff, k, k, h->sb.cap, h->sb.idx, h->sb.wt, h->sb.counts + 2, nullptr, 0.0, h->Gs_d,
+             h->Gs_f, h->ws, h->counters + 5, h->st));
+  if (rule == SYMNMF_RULE_HALS)
+    TRY(hals_update(Fu, Ff, n, k, 1, h->Gs_f, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART,
+                    h->ws, h->counters + 1, h->err, h->st));
+  else
+    TRY(bpp_rows(Fu, Ff, n, k, h->Gs_d, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART, h->ws,
+                 h->counters + 1, h->err, h->st));
+  return SYMNMF_OK;
+}
+
+static symnmf_status check_lvs(symnmf_t h, int rule) {
+  if (h->p.fmt != SYMNMF_X_CSR_F32 && h->p.fmt != SYMNMF_X_DENSE_F32 && h->p.fmt != SYMNMF_X_DENSE_F64)
+    return fail(h, SYMNMF_EUNSUPPORTED, "LvS needs CSR or dense F32/F64 X");
+  if (rule == SYMNMF_RULE_BPP && h->k > 16) return fail(h, SYMNMF_EUNSUPPORTED, "BPP rule needs k <= 16");
+  if (h->p.fmt != SYMNMF_X_CSR_F32 && h->k > 64) return SYMNMF_EUNSUPPORTED;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_lvs_update(symnmf_t h, int side, int rule) {
+  if (!h || (side != 0 && side != 1)) return SYMNMF_EINVAL;
+  TRYS(check_lvs(h, rule));
+  if (h->sample_side != side) return fail(h, SYMNMF_ESTATE, "lvs_update without a sample of that side");
+  TRYS(lvs_update_dev(h, side, rule));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_lvs_iterate(symnmf_t h, int iter0, int iters, double tau, int s, int rule) {
+  if (!h || iters < 0 || s < 0) return SYMNMF_EINVAL;
+  TRYS(check_lvs(h, rule));
+  TRYS(ensure_sampler(h, s));
+  for (int it = iter0; it < iter0 + iters; ++it) {
+    for (int side = 0; side < 2; ++side) {
+      TRYS(leverage_dev(h, side));
+      TRYS(sample_dev(h, side, it, tau, s));
+      TRYS(lvs_update_dev(h, side, rule));
+    }
+  }
+  TRYS(refresh_grams(h));
+  return SYMNMF_OK;
+}
+
+// -------------------------------------------------------------- residual
+
+extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double* surrogate,
+                                         double* proj_grad) {
+  if (!h) return SYMNMF_EINVAL;
+  TRYS(validate_sweep(h, source, SYMNMF_RULE_HALS));
+  const int k = h->k;
+  const int64_t n = h->n;
+  TRYS(refresh_grams(h));
+  auto apply_op = [&](const float* F, float* Yo) -> symnmf_status {
+    if (source == SYMNMF_SRC_LAI) {
+      TRY(xcross(h->U, h->l, h->l, F, k, k, n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf, h->ws,
+                 h->counters + 0, h->st));
+      TRY(apply_small(h->U, h->l, h->l, h->Mf, k, n, Yo, k, h->st));
+      return SYMNMF_OK;
+    }
+    return product(h, source, F, k, k, Yo, k);
+  };
+  TRYS(apply_op(h->H, h->Y));  // Y = X H
+  // part = (sum W .* XH, ||W - H||^2)
+  TRY(pair_reduce(h->W, h->Y, n * k, h->scal + S_PART2, h->ws, h->counters + 6, h->st));
+  TRY(pair_reduce(h->W, h->H, n * k, h->scal + S_PART3, h->ws, h->counters + 6, h->st));
+  TRY(objective(normx_for(h, source), h->Gd[1], h->Gd[0], k, h->scal + S_PART2, h->scal + S_ZERO,
+                h->scal + S_OBJ, nullptr, 0, h->st));
+  double pg2 = 0.0;
+  if (proj_grad) {
+    TRY(cudaMemsetAsync(h->scal + S_PG, 0, sizeof(double), h->st));
+    TRY(proj_grad_sq(h->W, h->H, h->Y, h->Gf[0], n, k, h->scal + S_ALPHA, h->scal + S_PG, h->st));
+    TRYS(apply_op(h->W, h->Y));  // Y = X W
+    TRY(proj_grad_sq(h->H, h->W, h->Y, h->Gf[1], n, k, h->scal + S_ALPHA, h->scal + S_PG, h->st));
+  }
+  double hs[S_COUNT];
+  TRY(cudaMemcpyAsync(hs, h->scal, sizeof(hs), cudaMemcpyDeviceToHost, h->st));
+  TRYS(check_device_error(h));
+  const double r2 = hs[S_OBJ];
+  const double nx2 = source == SYMNMF_SRC_LAI ? hs[S_LAI_NORM2]
+                     : source == SYMNMF_SRC_XHI ? hs[S_XHI_NORM2]
+                                                : hs[S_NORM2];
+  pg2 = hs[S_PG];
+  if (norm_resid) *norm_resid = sqrt(fmax(r2, 0.0) / nx2);
+  if (surrogate) *surrogate = r2 + h->alpha * hs[S_PART3 + 1];
+  if (proj_grad) *proj_grad = sqrt(pg2);
+  return SYMNMF_OK;
+}
+
+// ------------------------------------------------------- standalone kernels
+
+extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, const float* row_scale,
+                                         int64_t n, const float* F, int ldf, int N, float* Y, int ldy,
+                                         int gemm, void* stream) {
+  if (!x || !F || !Y || n < 1 || N < 1 || N > 256 || ldx < n || ldf < N || ldy < N) return SYMNMF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool tc = fmt == SYMNMF_X_DENSE_BF16 || fmt == SYMNMF_X_DENSE_FP8;
+  if (tc && gemm == SYMNMF_GEMM_SIMT) return SYMNMF_EUNSUPPORTED;
+  if (!tc && gemm == SYMNMF_GEMM_TC) return SYMNMF_EUNSUPPORTED;
+  if (!tc && N > 128) return SYMNMF_EINVAL;
+  if (fmt == SYMNMF_X_DENSE_FP8 && !row_scale) return SYMNMF_EINVAL;
+  cudaError_t e;
+  if (!tc) {
+    const size_t wsf = xf_simt_ws_floats(n, N);
+    float* ws = nullptr;
+    if (wsf && (e = cudaMallocAsync((void**)&ws, wsf * 4, st)) != cudaSuccess) return to_status(e);
+    e = xf_simt(fmt, x, ldx, n, F, ldf, N, Y, ldy, ws, wsf, st);
+    if (ws) cudaFreeAsync(ws, st);
+    return to_status(e);
+  }
+  const int BN = tc_block_n(N);
+  const int64_t ldp = (n + 15) / 16 * 16;
+  const size_t es = fmt == SYMNMF_X_DENSE_FP8 ? 1 : 2;
+  const size_t wsf = xf_tc_ws_floats(n, BN);
+  void* pack = nullptr;
+  float* ws = nullptr;
+  float* cs = nullptr;
+  unsigned* err = nullptr;
+  if ((e = cudaMallocAsync(&pack, (size_t)BN * ldp * es, st)) != cudaSuccess) return to_status(e);
+  if ((e = cudaMallocAsync((void**)&ws, wsf * 4, st)) != cudaSuccess) return to_status(e);
+  if ((e = cudaMallocAsync((void**)&cs, 256 * 4, st)) != cudaSuccess) return to_status(e);
+  if ((e = cudaMallocAsync((void**)&err, 4, st)) != cudaSuccess) return to_status(e);
+  cudaMemsetAsync(err, 0, 4, st);
+  if (fmt == SYMNMF_X_DENSE_BF16)
+    e = pack_ft_bf16(F, n, ldf, N, BN, pack, ldp, st);
+  else
+    e = pack_ft_fp8(F, n, ldf, N, BN, pack, ldp, cs, st);
+  if (e == cudaSuccess) e = xf_tc(fmt, x, ldx, row_scale, n, pack, ldp, cs, N, Y, ldy, ws, wsf, err, st);
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(pack, st);
+  cudaFreeAsync(ws, st);
+  cudaFreeAsync(cs, st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return to_status(e);
+  return herr ? SYMNMF_ETIMEOUT : SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                                       const float* F, int N, float* Y, void* stream) {
+  if (!row_ptr || !col || !val || !F || !Y || n < 1 || N < 1 || N > 128) return SYMNMF_EINVAL;
+  return to_status(csr_xf(row_ptr, col, val, n, F, N, N, Y, N, (cudaStream_t)stream));
+}
+
+extern "C" symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G, void* stream) {
+  if (!F || !G || n < 1 || N < 1 || N > 128) return SYMNMF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* ws = nullptr;
+  unsigned* cnt = nullptr;
+  const size_t wsd = xcross_ws_doubles(N, N);
+  cudaError_t e;
+  if ((e = cudaMallocAsync((void**)&ws, wsd * 8, st)) != cudaSuccess) return to_status(e);
+  if ((e = cudaMallocAsync((void**)&cnt, 4, st)) != cudaSuccess) return to_status(e);
+  cudaMemsetAsync(cnt, 0, 4, st);
+  e = xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, cnt, st);
+  cudaFreeAsync(ws, st);
+  cudaFreeAsync(cnt, st);
+  return to_status(e);
+}
+
+extern "C" symnmf_status symnmf_gaussian(float* out, int64_t n, int l, uint64_t seed, void* stream) {
+  if (!out || n < 1 || l < 1) return SYMNMF_EINVAL;
+  return to_status(philox_gaussian(out, n, l, seed, (cudaStream_t)stream));
+}
+
+extern "C" symnmf_status symnmf_quantize_fp8(const float* x, int64_t n, int64_t ldx, uint8_t* x8, int64_t ld8,
+                                             float* row_scale, void* stream) {
+  if (!x || !x8 || !row_scale || n < 1 || ldx < n || ld8 < n) return SYMNMF_EINVAL;
+  return to_status(quantize_fp8(x, n, ldx, x8, ld8, row_scale, (cudaStream_t)stream));
+}
+
+extern "C" symnmf_status symnmf_convert_bf16(const float* x, int64_t n, int64_t ldx, uint16_t* xb, int64_t ldb,
+                                             void* stream) {
+  if (!x || !xb || n < 1 || ldx < n || ldb < n) return SYMNMF_EINVAL;
+  return to_status(convert_bf16(x, n, ldx, xb, ldb, (cudaStream_t)stream));
+}

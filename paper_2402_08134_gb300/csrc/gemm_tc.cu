@@ -1,0 +1,424 @@
+// Dense Y = X F on the 5th-generation tensor cores (tcgen05) for BF16 or FP8
+// (E4M3, per-row scales of X and per-column scales of F) X, FP32 accumulation
+// in tensor memory.  This is the product that dominates SymNMF
+// ("products with X are the most expensive part", Section "Complexity" of
+// the LvS section) and the range finder of Alg. RRF.
+//
+// Layout: A = X (n x n, K-major rows, TMA tiles 128 x 128 bytes, 128-byte
+// swizzle), B = F^T packed (BN x n, K-major, same swizzle), D = 128 x BN FP32
+// in TMEM.  Warp roles per CTA (192 threads, one CTA per SM):
+//   warp 0      : TMA producer (one thread) into an STAGES-deep smem ring;
+//   warp 1      : TMEM allocator + MMA issuer (one thread);
+//   warps 2..5  : epilogue, tcgen05.ld of the accumulator -> FP32 partials.
+// Two TMEM accumulators alternate so that the epilogue of one tile overlaps
+// the MMAs of the next.
+//
+// Work split (stream-K): the (row tile, k block) iteration space is cut into
+// gridDim.x equal contiguous ranges, one per CTA, so every SM streams the
+// same number of X bytes.  A CTA writes one partial tile per row tile it
+// touches; a second kernel sums the partials of each row tile in CTA order
+// (deterministic) and applies the FP8 scales.
+//
+// Every mbarrier wait is bounded (%globaltimer, 2 s): on expiry the CTA sets
+// ERR_TIMEOUT, stops issuing work, drains its own copies and MMAs (again
+// bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace symnmf {
+
+template <int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = TC_BM * TC_ROW_BYTES;
+  static constexpr int B_BYTES = BN * TC_ROW_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (196 * 1024 / STAGE_BYTES) > 8 ? 8 : (196 * 1024 / STAGE_BYTES);
+  static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int BN, bool FP8>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    xf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 int kblocks, int64_t total_iters, float* __restrict__ partials, int max_segs,
+                 unsigned* err) {
+  using C = TcCfg<BN>;
+  constexpr int STAGES = C::STAGES;
+  constexpr int KSTEPS = TC_ROW_BYTES / 32;  // 32 bytes of K per MMA (16 bf16 / 32 e4m3)
+  constexpr int KELEMS = FP8 ? 128 : 64;     // elements of K per k block
+  constexpr uint32_t IDESC = make_idesc<FP8>(TC_BM, BN);
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * C::A_BYTES;
+  uint64_t* full = (uint64_t*)(sB + STAGES * C::B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t it0 = ((int64_t)blockIdx.x * total_iters) / gridDim.x;
+  const int64_t it1 = ((int64_t)(blockIdx.x + 1) * total_iters) / gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0;   // stages used at least once
+      uint32_t last_parity = 0;   // bit s: parity of the last fill of stage s
+      for (int64_t it = it0; it < it1; ++it) {
+        const int tile = (int)(it / kblocks);
+        const int kb = (int)(it - (int64_t)tile * kblocks);
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          set_error(err, ERR_TIMEOUT);
+          break;
+        }
+        mbar_expect_tx(&full[stage], C::STAGE_BYTES);
+        tma_load_2d(sA + stage * C::A_BYTES, &tmA, kb * KELEMS, tile * TC_BM, &full[stage]);
+        tma_load_2d(sB + stage * C::B_BYTES, &tmB, kb * KELEMS, 0, &full[stage]);
+        issued_mask |= 1u << stage;
+        last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      // drain: every copy this thread issued has landed before the CTA exits
+      for (int s = 0; s < STAGES; ++s)
+        if (issued_mask >> s & 1u) {
+          volatile int no_abort = 0;
+          mbar_wait(&full[s], (last_parity >> s) & 1u, &no_abort);
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int seg = 0;
+      bool ok = true;
+      int64_t it = it0;
+      while (ok && it < it1) {
+        const int64_t tile = it / kblocks;
+        const int64_t seg_end = min(it1, (tile + 1) * kblocks);
+        const int a = seg & 1;
+        const uint32_t use = (uint32_t)(seg >> 1);
+        if (!mbar_wait(&tempty[a], (use & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(a * BN);
+        const int64_t seg_begin = it;
+        for (; it < seg_end; ++it) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + stage * C::A_BYTES);
+          const uint32_t b0 = smem_u32(sB + stage * C::B_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ++ks)
+            umma<FP8>(d, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), IDESC,
+                      (it > seg_begin || ks > 0) ? 1u : 0u);
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[a]);
+        ++seg;
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        set_error(err, ERR_TIMEOUT);
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      umma_commit(done);
+      volatile int no_abort = 0;
+      mbar_wait(done, 0, &no_abort);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5)
+    const int ew = warp & 3;
+    const int row = ew * 32 + lane;
+    int seg = 0;
+    int64_t it = it0;
+    while (it < it1) {
+      const int64_t tile = it / kblocks;
+      const int64_t seg_end = min(it1, (tile + 1) * kblocks);
+      const int a = seg & 1;
+      const uint32_t use = (uint32_t)(seg >> 1);
+      if (!mbar_wait(&tfull[a], use & 1u, abort_flag)) {
+        *abort_flag = 1;
+        set_error(err, ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      float* dst = partials + (((size_t)blockIdx.x * max_segs + seg) * TC_BM + row) * BN;
+      const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)c, v);
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *(float4*)(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+      it = seg_end;
+      ++seg;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+}
+
+// Y[r, c] = (sum over the CTAs that covered row tile r / 128 of their partial)
+//           * row_scale[r] * col_scale[c]  (scales for FP8 only).
+__global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN,
+                                 int64_t kblocks, int64_t total, int G, int64_t n, int N, float* Y,
+                                 int ldy, const float* __restrict__ rs, const float* __restrict__ cs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * N) return;
+  const int64_t r = t / N;
+  const int c = (int)(t - r * N);
+  const int64_t tile = r / TC_BM;
+  const int64_t f_it = tile * kblocks, l_it = (tile + 1) * kblocks - 1;
+  const int64_t c0 = ((f_it + 1) * G - 1) / total;
+  const int64_t c1 = ((l_it + 1) * G - 1) / total;
+  float s = 0.f;
+  for (int64_t q = c0; q <= c1; ++q) {
+    const int64_t itb = (q * total) / G;
+    const int64_t seg = tile - itb / kblocks;
+    s += partials[((q * max_segs + seg) * TC_BM + (r - tile * TC_BM)) * BN + c];
+  }
+  if (rs) s *= rs[r] * cs[c];
+  Y[r * ldy + c] = s;
+}
+
+// ------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool tc_make_map(CUtensorMap* m, const void* base, bool fp8, uint64_t inner, uint64_t outer,
+                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int tc_block_n(int N) {
+  if (N <= 32) return 32;
+  if (N <= 64) return 64;
+  if (N <= 128) return 128;
+  return 256;
+}
+
+struct TcPlan {
+  int G, kblocks, mtiles, max_segs;
+  int64_t total;
+};
+
+static TcPlan tc_plan(int64_t n, bool fp8) {
+  TcPlan p;
+  const int kel = fp8 ? 128 : 64;
+  p.kblocks = (int)((n + kel - 1) / kel);
+  p.mtiles = (int)((n + TC_BM - 1) / TC_BM);
+  p.total = (int64_t)p.kblocks * p.mtiles;
+  p.G = (int)std::min<int64_t>(num_sms(), p.total);
+  p.max_segs = 1;
+  for (int c = 0; c < p.G; ++c) {
+    const int64_t a = ((int64_t)c * p.total) / p.G, b = ((int64_t)(c + 1) * p.total) / p.G;
+    const int segs = (int)((b - 1) / p.kblocks - a / p.kblocks + 1);
+    if (segs > p.max_segs) p.max_segs = segs;
+  }
+  return p;
+}
+
+size_t xf_tc_ws_floats(int64_t n, int BN) {
+  // the BF16 plan has the most k blocks, hence the most segments
+  const TcPlan p = tc_plan(n, false);
+  const TcPlan q = tc_plan(n, true);
+  const int segs = p.max_segs > q.max_segs ? p.max_segs : q.max_segs;
+  return (size_t)p.G * segs * TC_BM * BN;
+}
+
+__global__ void pack_ft_bf16_kernel(const float* F, int64_t n, int ldf, int N, int Npad,
+                                    __nv_bfloat16* out, int64_t ldp) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)Npad * ldp) return;
+  const int64_t c = t / ldp, i = t - c * ldp;
+  const float v = (c < N && i < n) ? F[i * ldf + c] : 0.f;
+  out[t] = __float2bfloat16_rn(v);
+}
+
+cudaError_t pack_ft_bf16(const float* F, int64_t n, int ldf, int N, int Npad, void* out, int64_t ldp,
+                         cudaStream_t st) {
+  const int64_t work = (int64_t)Npad * ldp;
+  pack_ft_bf16_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(F, n, ldf, N, Npad,
+                                                                 (__nv_bfloat16*)out, ldp);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void colmax_kernel(const float* F, int64_t n, int ldf, int N, float* cs) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x;
+  float m = 0.f;
+  if (c < N)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(F[i * ldf + c]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, sh[w]);
+    cs[c] = t > 0.f ? t / 448.0f : 1.0f;
+  }
+}
+
+__global__ void pack_ft_fp8_kernel(const float* F, int64_t n, int ldf, int N, int Npad, uint8_t* out,
+                                   int64_t ldp, const float* cs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)Npad * ldp) return;
+  const int64_t c = t / ldp, i = t - c * ldp;
+  const float v = (c < N && i < n) ? F[i * ldf + c] / cs[c] : 0.f;
+  const __nv_fp8_e4m3 q(v);
+  out[t] = q.__x;
+}
+
+cudaError_t pack_ft_fp8(const float* F, int64_t n, int ldf, int N, int Npad, void* out, int64_t ldp,
+                        float* col_scale, cudaStream_t st) {
+  colmax_kernel<<<Npad, 256, 0, st>>>(F, n, ldf, N, col_scale);
+  const int64_t work = (int64_t)Npad * ldp;
+  pack_ft_fp8_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(F, n, ldf, N, Npad, (uint8_t*)out, ldp,
+                                                                col_scale);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+template <int BN, bool FP8>
+static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
+                             unsigned* err, cudaStream_t st) {
+  using C = TcCfg<BN>;
+  cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       C::SMEM);
+  if (e != cudaSuccess) return e;
+  xf_tc_kernel<BN, FP8><<<p.G, TC_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, int64_t n,
+                  const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y, int ldy,
+                  float* ws, size_t ws_floats, unsigned* err, cudaStream_t st) {
+  const bool fp8 = fmt == 3;
+  if (!fp8 && fmt != 2) return cudaErrorInvalidValue;
+  const int BN = tc_block_n(N);
+  if (N > 256) return cudaErrorInvalidValue;
+  const size_t es = fp8 ? 1 : 2;
+  // TMA: 16-byte aligned bases and row pitches
+  if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
+    return cudaErrorInvalidValue;
+  const TcPlan p = tc_plan(n, fp8);
+  if (ws_floats < (size_t)p.G * p.max_segs * TC_BM * BN) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  const uint32_t kel = fp8 ? 128 : 64;
+  if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)n, (uint64_t)ldx * es, kel, TC_BM))
+    return cudaErrorInvalidValue;
+  if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel, (uint32_t)BN))
+    return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (fp8) {
+    switch (BN) {
+      case 32: e = launch_tc<32, true>(ma, mb, p, ws, err, st); break;
+      case 64: e = launch_tc<64, true>(ma, mb, p, ws, err, st); break;
+      case 128: e = launch_tc<128, true>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<256, true>(ma, mb, p, ws, err, st); break;
+    }
+  } else {
+    switch (BN) {
+      case 32: e = launch_tc<32, false>(ma, mb, p, ws, err, st); break;
+      case 64: e = launch_tc<64, false>(ma, mb, p, ws, err, st); break;
+      case 128: e = launch_tc<128, false>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<256, false>(ma, mb, p, ws, err, st); break;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  const int64_t work = n * N;
+  tc_reduce_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(
+      ws, p.max_segs, BN, p.kblocks, p.total, p.G, n, N, Y, ldy, fp8 ? row_scale : nullptr,
+      fp8 ? col_scale : nullptr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace symnmf

@@ -1,0 +1,86 @@
+// Solver handle layout (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/symnmf.h"
+#include "kernels.h"
+
+namespace symnmf {
+
+// Slots of the per-handle device scalar array.
+enum {
+  S_ALPHA = 0,
+  S_NORM2 = 1,      // ||X||_F^2
+  S_LAI_NORM2 = 2,  // sum lambda^2 = ||U Lambda U^T||_F^2
+  S_MAX = 3,        // xstats: max, sum, sum of squares (S_MAX .. S_MAX + 2)
+  S_MEAN = 6,
+  S_PART = 7,       // 2 slots: sum F_new .* Y, ||F_new - F_fix||^2
+  S_PART2 = 9,      // 2 slots
+  S_PART3 = 11,     // 2 slots
+  S_PG = 13,
+  S_OBJ = 14,
+  S_ZERO = 15,      // stays 0
+  S_XHI_MAX = 16,   // 3 slots for the float32 copy
+  S_XHI_NORM2 = 18,
+  S_COUNT = 24
+};
+constexpr int OBJ_RING = 4096;
+
+symnmf_status to_status(cudaError_t e);
+
+}  // namespace symnmf
+
+struct symnmf_ctx {
+  symnmf_problem p{};
+  symnmf_options o{};
+  cudaStream_t st = nullptr;
+  int64_t n = 0, ldx = 0, ldx_hi = 0, ldp = 0;
+  int k = 0;
+  double alpha = 0.0, normX2 = 0.0;
+  std::string msg;
+  std::vector<void*> allocs;
+
+  float *H = nullptr, *W = nullptr, *Y = nullptr;
+  double* Gd[2] = {nullptr, nullptr};  // [0] H^T H, [1] W^T W (FP64)
+  float* Gf[2] = {nullptr, nullptr};
+  double* Gs_d = nullptr;  // sampled / scratch Gram
+  float* Gs_f = nullptr;
+  double* scal = nullptr;
+  double* obj_ring = nullptr;
+  int* obj_cnt = nullptr;
+  double* ws = nullptr;
+  size_t ws_doubles = 0;
+  unsigned* counters = nullptr;  // last-block counters, one per launch site family
+  unsigned* err = nullptr;       // device error word
+  float* gemm_ws = nullptr;
+  size_t gemm_ws_floats = 0;
+  void* fpack = nullptr;
+  size_t fpack_bytes = 0;
+  float* colscale = nullptr;
+
+  // LAI
+  int l = 0, lai_cap = 0, lai_version = 0;
+  bool lai_ready = false;
+  float *Om = nullptr, *Qa = nullptr, *Qb = nullptr, *U = nullptr, *Mf = nullptr;
+  double *Sm_d = nullptr, *V_d = nullptr, *lam = nullptr, *ev = nullptr;
+  float *Sm_f = nullptr, *Rl_f = nullptr;
+
+  // LvS
+  symnmf::SampleBufs sb{};
+  double* Rinv_d = nullptr;
+  float* Rinv_f = nullptr;
+  int sample_side = -1;
+
+  // recorded sweep bodies
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int src = -1, rule = -1, lai_version = -1;
+    uint64_t nkernels = 0;
+  } graphs[6];
+  bool capturing = false;
+  cudaStream_t cap_st = nullptr;
+};

@@ -1,0 +1,794 @@
+// Row-streaming kernels of the SymNMF hot path: cross products / Grams with
+// FP64 accumulation, the fused regularised HALS update (Eq. symhals_update2),
+// LAI expansion Y = U (Lambda U^T F) (Alg. LAI-SymNMF), leverage-score row
+// pass (Alg. LvS-SymNMF), objective and projected-gradient reductions, and
+// the Philox generators.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace symnmf {
+
+// ---------------------------------------------------------------- xstats
+
+// Last-block-done reduction of per-block partials: no block ever waits.
+template <int NV>
+__device__ bool last_block(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ __forceinline__ double load_x(int fmt, const void* x, int64_t ldx, const float* rs,
+                                         int64_t i, int64_t j) {
+  switch (fmt) {
+    case 0: return ((const double*)x)[i * ldx + j];
+    case 1: return (double)((const float*)x)[i * ldx + j];
+    case 2: return (double)__bfloat162float(((const __nv_bfloat16*)x)[i * ldx + j]);
+    case 3: {
+      __nv_fp8_e4m3 v;
+      v.__x = ((const uint8_t*)x)[i * ldx + j];
+      return (double)rs[i] * (double)float(v);
+    }
+  }
+  return 0.0;
+}
+
+__global__ void xstats_dense_kernel(int fmt, const void* x, int64_t ldx, const float* rs, int64_t n,
+                                    double* out, double* ws, unsigned* counter) {
+  __shared__ double sh[32];
+  double mx = -INFINITY, sm = 0.0, sq = 0.0;
+  const int64_t total = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const double v = load_x(fmt, x, ldx, rs, i, j);
+    mx = fmax(mx, v);
+    sm += v;
+    sq += v * v;
+  }
+  // block reductions (max via negation trick is not needed: use warp_max)
+  mx = warp_max(mx);
+  __shared__ double shm[32];
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? shm[threadIdx.x] : -INFINITY;
+    mx = warp_max(t);
+  }
+  sm = block_sum(sm, sh);
+  sq = block_sum(sq, sh);
+  if (threadIdx.x == 0) {
+    ws[3 * blockIdx.x + 0] = mx;
+    ws[3 * blockIdx.x + 1] = sm;
+    ws[3 * blockIdx.x + 2] = sq;
+  }
+  if (last_block<1>(counter)) {
+    double M = -INFINITY;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) M = fmax(M, __ldcg(ws + 3 * b));
+    M = warp_max(M);
+    __shared__ double shx[32];
+    if ((threadIdx.x & 31) == 0) shx[threadIdx.x >> 5] = M;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, shx[w]);
+      out[0] = M;
+    }
+    reduce_partials(ws + 1, 3, 2, gridDim.x, out + 1, sh);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+__global__ void xstats_csr_kernel(const float* val, int64_t nnz, double* out, double* ws,
+                                  unsigned* counter) {
+  __shared__ double sh[32];
+  double mx = -INFINITY, sm = 0.0, sq = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = val[e];
+    mx = fmax(mx, v);
+    sm += v;
+    sq += v * v;
+  }
+  mx = warp_max(mx);
+  __shared__ double shm[32];
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? shm[threadIdx.x] : -INFINITY;
+    mx = warp_max(t);
+  }
+  sm = block_sum(sm, sh);
+  sq = block_sum(sq, sh);
+  if (threadIdx.x == 0) {
+    ws[3 * blockIdx.x + 0] = mx;
+    ws[3 * blockIdx.x + 1] = sm;
+    ws[3 * blockIdx.x + 2] = sq;
+  }
+  if (last_block<1>(counter)) {
+    double M = -INFINITY;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) M = fmax(M, __ldcg(ws + 3 * b));
+    M = warp_max(M);
+    __shared__ double shx[32];
+    if ((threadIdx.x & 31) == 0) shx[threadIdx.x >> 5] = M;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, shx[w]);
+      out[0] = M;
+    }
+    reduce_partials(ws + 1, 3, 2, gridDim.x, out + 1, sh);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+cudaError_t xstats(int fmt, const void* x, int64_t ldx, const float* row_scale, int64_t n,
+                   const int64_t* row_ptr, int64_t nnz, double* out, double* ws, unsigned* counter,
+                   cudaStream_t st) {
+  (void)row_ptr;
+  const int grid = num_sms() * 4;
+  if (fmt == 4)
+    xstats_csr_kernel<<<grid, 256, 0, st>>>((const float*)x, nnz, out, ws, counter);
+  else
+    xstats_dense_kernel<<<grid, 256, 0, st>>>(fmt, x, ldx, row_scale, n, out, ws, counter);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- cross product
+
+constexpr int XC_THREADS = 256;
+constexpr int XC_CHUNK = 32;
+
+size_t xcross_ws_doubles(int la, int lb) { return (size_t)2 * num_sms() * la * lb + 64; }
+
+// C = A^T diag(wt) B over (gathered) rows.  FP32 products accumulate over a
+// chunk of XC_CHUNK rows, then into FP64 per-thread sums; block partials are
+// summed in block order by the last block (deterministic).
+template <int TPT>
+__global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
+    const float* __restrict__ A, int lda, int la, const float* __restrict__ B, int ldb, int lb,
+    int64_t n, const int32_t* __restrict__ idx, const float* __restrict__ wt, const int* cnt,
+    const double* __restrict__ lam, double shift, double* C, float* Cf, double* ws,
+    unsigned* counter) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int la4 = (la + 3) & ~3, lb4 = (lb + 3) & ~3;
+  float* As = (float*)smraw;
+  float* Bs = As + XC_CHUNK * la4;
+  double* red = (double*)(Bs + XC_CHUNK * lb4);
+  const int ta = la4 >> 2, tb = lb4 >> 2, T = ta * tb;
+  const int tid = threadIdx.x;
+  const int R = T >= XC_THREADS ? 1 : XC_THREADS / T;
+  const int rg = T >= XC_THREADS ? 0 : tid / T;
+  const bool active = rg < R;
+
+  const int64_t count = cnt ? (int64_t)(*cnt) : n;
+  int64_t per = (count + gridDim.x - 1) / gridDim.x;
+  per = (per + XC_CHUNK - 1) / XC_CHUNK * XC_CHUNK;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(count, r0 + per);
+
+  double acc[TPT][16];
+#pragma unroll
+  for (int t = 0; t < TPT; ++t)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[t][e] = 0.0;
+
+  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK) {
+    // stage the chunk
+    for (int e = tid; e < XC_CHUNK * la4; e += XC_THREADS) {
+      const int rr = e / la4, c = e - rr * la4;
+      const int64_t r = rb + rr;
+      float v = 0.f;
+      if (r < r1 && c < la) {
+        const int64_t src = idx ? (int64_t)idx[r] : r;
+        v = A[src * lda + c];
+      }
+      As[e] = v;
+    }
+    for (int e = tid; e < XC_CHUNK * lb4; e += XC_THREADS) {
+      const int rr = e / lb4, c = e - rr * lb4;
+      const int64_t r = rb + rr;
+      float v = 0.f;
+      if (r < r1 && c < lb) {
+        const int64_t src = idx ? (int64_t)idx[r] : r;
+        v = B[src * ldb + c];
+        if (wt) v *= wt[r];
+      }
+      Bs[e] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int t = 0; t < TPT; ++t) {
+        const int tile = (T >= XC_THREADS) ? tid + t * XC_THREADS : tid % T;
+        if (tile < T) {
+          const int ti = tile / tb, tj = tile - ti * tb;
+          float f[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) f[e] = 0.f;
+          for (int rr = rg; rr < XC_CHUNK; rr += R) {
+            const float4 a = *(const float4*)(As + rr * la4 + 4 * ti);
+            const float4 b = *(const float4*)(Bs + rr * lb4 + 4 * tj);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) f[p * 4 + q] = fmaf(av[p], bv[q], f[p * 4 + q]);
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[t][e] += (double)f[e];
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // combine row groups (sequentially, fixed order) and write the block partial
+  const int LL = la * lb;
+  if (R > 1) {
+    for (int g = 0; g < R; ++g) {
+      if (active && rg == g) {
+        const int tile = tid % T;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) red[tile * 16 + e] = (g == 0 ? 0.0 : red[tile * 16 + e]) + acc[0][e];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < T * 16; e += XC_THREADS) {
+      const int tile = e >> 4, w = e & 15;
+      const int i = (tile / tb) * 4 + (w >> 2), j = (tile % tb) * 4 + (w & 3);
+      if (i < la && j < lb) ws[(size_t)blockIdx.x * LL + i * lb + j] = red[e];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+      const int tile = tid + t * XC_THREADS;
+      if (tile < T) {
+        const int ti = tile / tb, tj = tile - ti * tb;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int i = ti * 4 + (e >> 2), j = tj * 4 + (e & 3);
+          if (i < la && j < lb) ws[(size_t)blockIdx.x * LL + i * lb + j] = acc[t][e];
+        }
+      }
+    }
+  }
+  if (last_block<1>(counter)) {
+    const unsigned G = gridDim.x;
+    for (int e = tid; e < LL; e += XC_THREADS) {
+      // four independent chains keep several L2 loads in flight (fixed order)
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      unsigned b = 0;
+      for (; b + 4 <= G; b += 4) {
+        s0 += __ldcg(ws + (size_t)b * LL + e);
+        s1 += __ldcg(ws + (size_t)(b + 1) * LL + e);
+        s2 += __ldcg(ws + (size_t)(b + 2) * LL + e);
+        s3 += __ldcg(ws + (size_t)(b + 3) * LL + e);
+      }
+      for (; b < G; ++b) s0 += __ldcg(ws + (size_t)b * LL + e);
+      double s = (s0 + s1) + (s2 + s3);
+      const int i = e / lb, j = e - i * lb;
+      if (lam) s *= lam[i];
+      if (i == j) s += shift;
+      if (C) C[e] = s;
+      if (Cf) Cf[e] = (float)s;
+    }
+    if (tid == 0) *counter = 0;
+  }
+}
+
+cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int lb, int64_t n,
+                   const int32_t* idx, const float* wt, const int* cnt, const double* lam,
+                   double shift, double* C, float* Cf, double* ws, unsigned* counter,
+                   cudaStream_t st) {
+  if (la < 1 || lb < 1 || la > 128 || lb > 128) return cudaErrorInvalidValue;
+  const int la4 = (la + 3) & ~3, lb4 = (lb + 3) & ~3;
+  const int T = (la4 / 4) * (lb4 / 4);
+  const size_t smem = (size_t)XC_CHUNK * (la4 + lb4) * 4 + (size_t)(T < XC_THREADS ? T : 0) * 16 * 8;
+  int grid = (int)((n + 255) / 256);
+  const int cap = num_sms() * ((size_t)la * lb <= 4096 ? 2 : 1);
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  cudaError_t e;
+  if (T <= XC_THREADS) {
+    e = cudaFuncSetAttribute(xcross_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    xcross_kernel<1><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
+                                                     shift, C, Cf, ws, counter);
+  } else if (T <= 2 * XC_THREADS) {
+    e = cudaFuncSetAttribute(xcross_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    xcross_kernel<2><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
+                                                     shift, C, Cf, ws, counter);
+  } else {
+    e = cudaFuncSetAttribute(xcross_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    xcross_kernel<4><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
+                                                     shift, C, Cf, ws, counter);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ HALS
+
+constexpr int HALS_ROWS = 64;  // rows per tile = threads per block
+
+// One thread per row.  Per group g (k columns, its own Gram G_g):
+//   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
+// i = 0..k-1 in order with the columns already updated (Eq. symhals_update2).
+template <int KMAX>
+__global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
+    float* __restrict__ Fu, const float* __restrict__ Ff, int64_t n, int k, int ng,
+    const float* __restrict__ G, float alpha, const float* __restrict__ Y, int ldy,
+    const float* __restrict__ U, int l, const float* __restrict__ M, double* part, double* ws,
+    unsigned* counter, unsigned* err) {
+  extern __shared__ __align__(16) float sm[];
+  const int RW = ng * k;         // row width
+  const int P = RW + 1;          // padded smem row stride
+  float* Gs = sm;                // ng*k*k
+  float* inv = Gs + ng * k * k;  // ng*k
+  float* Ys = inv + ng * k;      // HALS_ROWS * P
+  float* Hs = Ys + HALS_ROWS * P;
+  float* Ws = Hs + HALS_ROWS * P;
+  float* Us = Ws + HALS_ROWS * P;  // HALS_ROWS * (l+1)   (LAI only)
+  float* Ms = Us + (U ? HALS_ROWS * (l + 1) : 0);  // l * RW (LAI only)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < ng * k * k; e += HALS_ROWS) Gs[e] = G[e];
+  __syncthreads();
+  for (int e = tid; e < ng * k; e += HALS_ROWS) {
+    const int g = e / k, i = e - g * k;
+    inv[e] = 1.0f / (Gs[g * k * k + i * k + i] + alpha);
+  }
+  if (U)
+    for (int e = tid; e < l * RW; e += HALS_ROWS) Ms[e] = M[e];
+  __syncthreads();
+
+  double tr = 0.0, dd = 0.0;
+  bool bad = false;
+  const int64_t ntiles = (n + HALS_ROWS - 1) / HALS_ROWS;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t base = tile * HALS_ROWS;
+    const int rows = (int)min((int64_t)HALS_ROWS, n - base);
+    // coalesced staging of the tile's rows
+    for (int e = tid; e < rows * RW; e += HALS_ROWS) {
+      const int rr = e / RW, c = e - rr * RW;
+      Hs[rr * P + c] = Ff[(base + rr) * RW + c];
+      Ws[rr * P + c] = Fu[(base + rr) * RW + c];
+      if (!U) Ys[rr * P + c] = Y[(base + rr) * (int64_t)ldy + c];
+    }
+    if (U)
+      for (int e = tid; e < rows * l; e += HALS_ROWS) {
+        const int rr = e / l, c = e - rr * l;
+        Us[rr * (l + 1) + c] = U[(base + rr) * (int64_t)l + c];
+      }
+    __syncthreads();
+    if (tid < rows) {
+      float* yr = Ys + tid * P;
+      const float* hr = Hs + tid * P;
+      float* wr = Ws + tid * P;
+      if (U) {  // Y_r = U_r M  (LAI product fused into the update)
+        const float* ur = Us + tid * (l + 1);
+        for (int c = 0; c < RW; ++c) yr[c] = 0.f;
+        for (int p = 0; p < l; ++p) {
+          const float u = ur[p];
+          const float* mrow = Ms + p * RW;
+          for (int c = 0; c < RW; ++c) yr[c] = fmaf(u, mrow[c], yr[c]);
+        }
+      }
+      for (int g = 0; g < ng; ++g) {
+        const float* Gg = Gs + g * k * k;
+        const int o = g * k;
+        float w[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) w[j] = j < k ? wr[o + j] : 0.f;
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i) {
+          if (i < k) {
+            float acc = fmaf(alpha, hr[o + i], yr[o + i]);
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+              if (j != i && j < k) acc = fmaf(-w[j], Gg[j * k + i], acc);
+            w[i] = fmaxf(acc * inv[o + i], 0.f);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j < k) {
+            if (!isfinite(w[j])) bad = true;
+            wr[o + j] = w[j];
+            tr += (double)w[j] * (double)yr[o + j];
+            const float d = w[j] - hr[o + j];
+            dd += (double)d * (double)d;
+          }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * RW; e += HALS_ROWS) {
+      const int rr = e / RW, c = e - rr * RW;
+      Fu[(base + rr) * RW + c] = Ws[rr * P + c];
+    }
+    __syncthreads();
+  }
+  if (bad) set_error(err, ERR_NAN);
+  __shared__ double sh[32];
+  tr = block_sum(tr, sh);
+  dd = block_sum(dd, sh);
+  if (tid == 0) {
+    ws[2 * blockIdx.x] = tr;
+    ws[2 * blockIdx.x + 1] = dd;
+  }
+  if (last_block<1>(counter)) {
+    reduce_partials(ws, 2, 2, gridDim.x, part, sh);
+    if (tid == 0) *counter = 0;
+  }
+}
+
+template <int KMAX>
+static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, int ng, const float* G,
+                               double alpha, const float* Y, int ldy, const float* U, int l,
+                               const float* M, double* part, double* ws, unsigned* counter,
+                               unsigned* err, cudaStream_t st) {
+  const int RW = ng * k, P = RW + 1;
+  size_t smem = (size_t)(ng * k * k + ng * k + 3 * HALS_ROWS * P) * 4;
+  if (U) smem += (size_t)(HALS_ROWS * (l + 1) + l * RW) * 4;
+  cudaError_t e = cudaFuncSetAttribute(hals_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (n + HALS_ROWS - 1) / HALS_ROWS;
+  int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 8);
+  if (grid < 1) grid = 1;
+  hals_kernel<KMAX><<<grid, HALS_ROWS, smem, st>>>(Fu, Ff, n, k, ng, G, (float)alpha, Y, ldy, U, l, M,
+                                                   part, ws, counter, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t hals_update(float* F_upd, const float* F_fix, int64_t n, int k, int ngroups,
+                        const float* G, double alpha, const float* Y, int ldy, const float* U, int l,
+                        const float* M, double* part, double* ws, unsigned* counter, unsigned* err,
+                        cudaStream_t st) {
+  if (k <= 8)
+    return launch_hals<8>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+  if (k <= 16)
+    return launch_hals<16>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+  if (k <= 32)
+    return launch_hals<32>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+  if (k <= 64)
+    return launch_hals<64>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ apply_small
+
+__global__ void apply_small_kernel(const float* __restrict__ A, int lda, int la,
+                                   const float* __restrict__ B, int lb, int64_t n, float* out,
+                                   int ldo) {
+  extern __shared__ float Bsh[];
+  for (int e = threadIdx.x; e < la * lb; e += blockDim.x) Bsh[e] = B[e];
+  __syncthreads();
+  const int chunks = (lb + 15) / 16;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * chunks) return;
+  const int64_t i = t / chunks;
+  const int c0 = (int)(t - i * chunks) * 16;
+  float acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+  for (int c = 0; c < la; ++c) {
+    const float a = A[i * lda + c];
+    const float* b = Bsh + c * lb + c0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (c0 + j < lb) acc[j] = fmaf(a, b[j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (c0 + j < lb) out[i * ldo + c0 + j] = acc[j];
+}
+
+cudaError_t apply_small(const float* A, int lda, int la, const float* B, int lb, int64_t n,
+                        float* out, int ldo, cudaStream_t st) {
+  const size_t smem = (size_t)la * lb * 4;
+  cudaError_t e = cudaFuncSetAttribute(apply_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t work = n * ((lb + 15) / 16);
+  const int grid = (int)((work + 255) / 256);
+  apply_small_kernel<<<grid, 256, smem, st>>>(A, lda, la, B, lb, n, out, ldo);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- leverage
+
+template <int KMAX>
+__global__ void leverage_kernel(const float* __restrict__ F, int64_t n, int k,
+                                const float* __restrict__ Rinv, double* lev) {
+  __shared__ float Rs[KMAX * KMAX];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rs[e] = Rinv[e];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float h[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) h[j] = j < k ? F[i * k + j] : 0.f;
+  float s = 0.f;
+  // z_j = sum_{p <= j} h_p Rinv[p][j]  (Rinv upper triangular)
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      float z = 0.f;
+#pragma unroll
+      for (int p = 0; p <= j; ++p) z = fmaf(h[p], Rs[p * k + j], z);
+      s = fmaf(z, z, s);
+    }
+  }
+  lev[i] = (double)s;
+}
+
+cudaError_t leverage_rows(const float* F, int64_t n, int k, const float* Rinv, double* lev,
+                          cudaStream_t st) {
+  const int grid = (int)((n + 127) / 128);
+  if (k <= 16)
+    leverage_kernel<16><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+  else if (k <= 32)
+    leverage_kernel<32><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+  else if (k <= 64)
+    leverage_kernel<64><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+  else
+    return cudaErrorInvalidValue;
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- objective
+
+__global__ void objective_kernel(const double* normX2, const double* Ga, const double* Gb, int k,
+                                 const double* part, const double* alpha, double* out, int* cnt,
+                                 int cap) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) s += Ga[e] * Gb[e];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double v = normX2[0] + s - 2.0 * part[0] + alpha[0] * part[1];
+    if (cnt) {
+      const int t = *cnt;
+      if (t < cap) out[t] = v;
+      *cnt = t + 1;
+    } else {
+      out[0] = v;
+    }
+  }
+}
+
+cudaError_t objective(const double* normX2, const double* Ga, const double* Gb, int k,
+                      const double* part, const double* alpha, double* out, int* cnt, int cap,
+                      cudaStream_t st) {
+  objective_kernel<<<1, 256, 0, st>>>(normX2, Ga, Gb, k, part, alpha, out, cnt, cap);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// out[0] = sum a .* b, out[1] = sum (a - b)^2 over `count` entries (FP64, last block finalises).
+__global__ void pair_reduce_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                   int64_t count, double* out, double* ws, unsigned* counter) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double x = a[t], y = b[t];
+    s0 += x * y;
+    s1 += (x - y) * (x - y);
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    ws[2 * blockIdx.x] = s0;
+    ws[2 * blockIdx.x + 1] = s1;
+  }
+  if (last_block<1>(counter)) {
+    reduce_partials(ws, 2, 2, gridDim.x, out, sh);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+cudaError_t pair_reduce(const float* a, const float* b, int64_t count, double* out, double* ws,
+                        unsigned* counter, cudaStream_t st) {
+  pair_reduce_kernel<<<num_sms() * 2, 256, 0, st>>>(a, b, count, out, ws, counter);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void sumsq_kernel(const double* v, int l, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < l; ++i) s += v[i] * v[i];
+    out[0] = s;
+  }
+}
+
+cudaError_t sumsq(const double* v, int l, double* out, cudaStream_t st) {
+  sumsq_kernel<<<1, 32, 0, st>>>(v, l, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- projected gradient
+
+__global__ void proj_grad_kernel(const float* __restrict__ F, const float* __restrict__ O,
+                                 const float* __restrict__ Y, const float* __restrict__ Gm,
+                                 int64_t n, int k, const double* alpha, double* acc) {
+  extern __shared__ float Gs[];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Gs[e] = Gm[e];
+  __syncthreads();
+  const float a = (float)alpha[0];
+  double s = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / k;
+    const int c = (int)(t - i * k);
+    float g = 0.f;
+    for (int j = 0; j < k; ++j) g = fmaf(F[i * k + j], Gs[j * k + c], g);
+    const float f = F[t];
+    const double grad = 2.0 * ((double)g - (double)Y[t]) + 2.0 * (double)a * ((double)f - (double)O[t]);
+    if (grad < 0.0 || f > 0.f) s += grad * grad;
+  }
+  __shared__ double sh[32];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
+cudaError_t proj_grad_sq(const float* F, const float* Other, const float* Y, const float* Gother,
+                         int64_t n, int k, const double* alpha, double* acc, cudaStream_t st) {
+  const int grid = num_sms() * 4;
+  proj_grad_kernel<<<grid, 256, (size_t)k * k * 4, st>>>(F, Other, Y, Gother, n, k, alpha, acc);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- generators
+
+// Omega[i, 2p], Omega[i, 2p+1] from Philox counter (p, i lo, i hi, TAG_OMEGA):
+// u1 = (x0 + 1) 2^-32, u2 = x1 2^-32, Box-Muller in double.
+__global__ void gaussian_kernel(float* out, int64_t n, int l, uint32_t k0, uint32_t k1) {
+  const int np = (l + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * np) return;
+  const int64_t i = t / np;
+  const int p = (int)(t - i * np);
+  const Philox4 r = philox4x32_10((uint32_t)p, (uint32_t)i, (uint32_t)(i >> 32), TAG_OMEGA, k0, k1);
+  const double u1 = ((double)r.x0 + 1.0) * 0x1p-32;
+  const double u2 = (double)r.x1 * 0x1p-32;
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  out[i * l + 2 * p] = (float)(rad * c);
+  if (2 * p + 1 < l) out[i * l + 2 * p + 1] = (float)(rad * s);
+}
+
+cudaError_t philox_gaussian(float* out, int64_t n, int l, uint64_t seed, cudaStream_t st) {
+  const int64_t work = n * ((l + 1) / 2);
+  gaussian_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(out, n, l, (uint32_t)seed,
+                                                             (uint32_t)(seed >> 32));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// H[i, j] = x0 2^-32 * scale, counter (j, i lo, i hi, TAG_INIT); scale =
+// scale_mul * sqrt(scale_num[0]) when scale_num != NULL, else 1.
+__global__ void uniform_kernel(float* out, int64_t n, int k, uint32_t k0, uint32_t k1,
+                               const double* scale_num, double scale_mul) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t / k;
+  const int j = (int)(t - i * k);
+  const Philox4 r = philox4x32_10((uint32_t)j, (uint32_t)i, (uint32_t)(i >> 32), TAG_INIT, k0, k1);
+  double v = (double)r.x0 * 0x1p-32;
+  if (scale_num) v *= scale_mul * sqrt(scale_num[0]);
+  out[t] = (float)v;
+}
+
+cudaError_t philox_uniform(float* out, int64_t n, int k, uint64_t seed, const double* scale_num,
+                           double scale_mul, cudaStream_t st) {
+  const int64_t work = n * k;
+  uniform_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(out, n, k, (uint32_t)seed,
+                                                            (uint32_t)(seed >> 32), scale_num,
+                                                            scale_mul);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void convert_bf16_kernel(const float* x, int64_t n, int64_t ldx, __nv_bfloat16* xb,
+                                    int64_t ldb) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ldb;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ldb, j = t - i * ldb;
+    xb[t] = __float2bfloat16_rn(j < n ? x[i * ldx + j] : 0.f);
+  }
+}
+
+cudaError_t convert_bf16(const float* x, int64_t n, int64_t ldx, uint16_t* xb, int64_t ldb,
+                         cudaStream_t st) {
+  convert_bf16_kernel<<<num_sms() * 8, 256, 0, st>>>(x, n, ldx, (__nv_bfloat16*)xb, ldb);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Per-row E4M3 quantisation: scale_i = max_j |X_ij| / 448 (1 for a zero row).
+__global__ void quantize_fp8_kernel(const float* x, int64_t n, int64_t ldx, uint8_t* x8, int64_t ld8,
+                                    float* rs) {
+  __shared__ float shm[32];
+  const int64_t i = blockIdx.x;
+  float m = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, fabsf(x[i * ldx + j]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? shm[threadIdx.x] : 0.f;
+    t = warp_max(t);
+    if (threadIdx.x == 0) shm[0] = t;
+  }
+  __syncthreads();
+  const float mx = shm[0];
+  const float scale = mx > 0.f ? mx / 448.0f : 1.0f;
+  const float invs = 1.0f / scale;
+  for (int64_t j = threadIdx.x; j < ld8; j += blockDim.x) {
+    const float v = j < n ? x[i * ldx + j] * invs : 0.f;
+    const __nv_fp8_e4m3 q(v);  // round to nearest, saturating to finite
+    x8[i * ld8 + j] = q.__x;
+  }
+  if (threadIdx.x == 0) rs[i] = scale;
+}
+
+cudaError_t quantize_fp8(const float* x, int64_t n, int64_t ldx, uint8_t* x8, int64_t ld8,
+                         float* row_scale, cudaStream_t st) {
+  quantize_fp8_kernel<<<(unsigned)n, 256, 0, st>>>(x, n, ldx, x8, ld8, row_scale);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void check_factor_kernel(const float* F, int64_t count, unsigned* flags) {
+  bool neg = false, bad = false;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float v = F[t];
+    if (!isfinite(v)) bad = true;
+    if (v < 0.f) neg = true;
+  }
+  if (neg) atomicOr(flags, 1u);
+  if (bad) atomicOr(flags, 2u);
+}
+
+cudaError_t check_factor(const float* F, int64_t count, unsigned* flags, cudaStream_t st) {
+  check_factor_kernel<<<num_sms() * 2, 256, 0, st>>>(F, count, flags);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void normalize_rows_kernel(const float* in, int64_t n, int l, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < l; ++c) s += (double)in[i * l + c] * in[i * l + c];
+  const float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
+  for (int c = 0; c < l; ++c) out[i * l + c] = in[i * l + c] * inv;
+}
+
+cudaError_t normalize_rows(const float* in, int64_t n, int l, float* out, cudaStream_t st) {
+  normalize_rows_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(in, n, l, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace symnmf

@@ -1,0 +1,241 @@
+// Single-CTA FP64 kernels on k x k / l x l matrices: Cholesky with explicit
+// triangular inverse (CholeskyQR of the LvS section, second CholeskyQR2 pass
+// of the range finder) and cyclic Jacobi eigen-decomposition (Alg. Apx-EVD,
+// T = Q_T Lambda Q_T^T, and the rank-safe first orthonormalisation pass).
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace symnmf {
+
+// A = G + shift I = R^T R (R upper), then Rinv = R^{-1}.  A pivot <= tol *
+// max diag is dropped (row/col of Rinv set to zero); in strict mode
+// (drop_tol <= 0) a pivot <= 0 also raises ERR_NOTSPD.
+__global__ void chol_inverse_kernel(const double* G, int k, double shift, double drop_tol,
+                                    double* Rinv, float* Rinv_f, unsigned* err) {
+  extern __shared__ double A[];  // k*k (becomes R), then X = R^{-1} k*k
+  double* X = A + k * k;
+  __shared__ int dropped[128];
+  __shared__ double maxdiag;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e - i * k;
+    A[e] = 0.5 * (G[i * k + j] + G[j * k + i]) + (i == j ? shift : 0.0);
+    X[e] = 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < k; ++i) m = fmax(m, A[i * k + i]);
+    maxdiag = m;
+  }
+  __syncthreads();
+  // shift < 0 means a shift relative to the largest diagonal entry
+  if (shift < 0.0) {
+    for (int i = tid; i < k; i += nt) A[i * k + i] += -shift * maxdiag;
+    __syncthreads();
+  }
+  const double tol = drop_tol > 0.0 ? drop_tol * maxdiag : 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      const double d = A[j * k + j];
+      if (d <= tol || !(d > 0.0)) {
+        dropped[j] = 1;
+        A[j * k + j] = 0.0;
+        if (drop_tol <= 0.0) set_error(err, ERR_NOTSPD);
+      } else {
+        dropped[j] = 0;
+        A[j * k + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double rjj = A[j * k + j];
+    const bool dj = dropped[j];
+    for (int c = j + 1 + tid; c < k; c += nt) A[j * k + c] = dj ? 0.0 : A[j * k + c] / rjj;
+    __syncthreads();
+    // trailing update of the upper triangle
+    const int m = k - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = j + 1 + e / m, c = j + 1 + e % m;
+      if (c >= r) A[r * k + c] -= A[j * k + r] * A[j * k + c];
+    }
+    __syncthreads();
+  }
+  // R^{-1} column by column (back substitution), one column per thread
+  for (int c = tid; c < k; c += nt) {
+    for (int i = c; i >= 0; --i) {
+      if (dropped[i]) {
+        X[i * k + c] = 0.0;
+        continue;
+      }
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int j = i + 1; j <= c; ++j) s -= A[i * k + j] * X[j * k + c];
+      X[i * k + c] = s / A[i * k + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e - i * k;
+    const double v = (j >= i) ? X[e] : 0.0;
+    if (Rinv) Rinv[e] = v;
+    if (Rinv_f) Rinv_f[e] = (float)v;
+  }
+}
+
+cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,
+                         float* Rinv_f, unsigned* err, cudaStream_t st) {
+  if (k < 1 || k > 128) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * k * k * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  chol_inverse_kernel<<<1, 256, smem, st>>>(G, k, shift, drop_tol, Rinv, Rinv_f, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Cyclic two-sided Jacobi with the round-robin (circle) ordering: each round
+// rotates l/2 disjoint pairs at once (Golub & Van Loan, symmetric Schur 2x2).
+__global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* lam) {
+  extern __shared__ double sm[];
+  const int L = (l + 1) & ~1;  // padded to even; index l is a dummy when l is odd
+  double* A = sm;              // l*l
+  double* V = A + l * l;       // l*l
+  double* cs = V + l * l;      // 2 * (L/2)
+  int* pp = (int*)(cs + L);    // L/2
+  int* qq = pp + L / 2;
+  __shared__ double off, tot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e / l, j = e - i * l;
+    A[e] = 0.5 * (Ain[i * l + j] + Ain[j * l + i]);
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int m = L / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    {
+      __shared__ double shr[32];
+      double o = 0.0, t = 0.0;
+      for (int e = tid; e < l * l; e += nt) {
+        const double v = A[e] * A[e];
+        t += v;
+        if (e / l != e % l) o += v;
+      }
+      o = block_sum(o, shr);
+      t = block_sum(t, shr);
+      if (tid == 0) {
+        off = o;
+        tot = t;
+      }
+    }
+    __syncthreads();
+    if (off <= 1e-28 * tot || off == 0.0) break;
+    for (int round = 0; round < L - 1; ++round) {
+      // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate
+      for (int i = tid; i < m; i += nt) {
+        const int a = (i == 0) ? 0 : ((i - 1 + round) % (L - 1)) + 1;
+        const int bslot = L - 1 - i;
+        const int b = ((bslot - 1 + round) % (L - 1)) + 1;
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < l) {
+          const double apq = A[p * l + q];
+          if (apq != 0.0) {
+            const double tau = (A[q * l + q] - A[p * l + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        } else {
+          p = -1;
+        }
+        pp[i] = p;
+        qq[i] = q;
+        cs[2 * i] = c;
+        cs[2 * i + 1] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < m * l; e += nt) {
+        const int i = e / l, col = e - i * l;
+        const int p = pp[i], q = qq[i];
+        if (p < 0) continue;
+        const double c = cs[2 * i], s = cs[2 * i + 1];
+        const double ap = A[p * l + col], aq = A[q * l + col];
+        A[p * l + col] = c * ap - s * aq;
+        A[q * l + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J and V <- V J
+      for (int e = tid; e < m * l; e += nt) {
+        const int i = e / l, row = e - i * l;
+        const int p = pp[i], q = qq[i];
+        if (p < 0) continue;
+        const double c = cs[2 * i], s = cs[2 * i + 1];
+        const double ap = A[row * l + p], aq = A[row * l + q];
+        A[row * l + p] = c * ap - s * aq;
+        A[row * l + q] = s * ap + c * aq;
+        const double vp = V[row * l + p], vq = V[row * l + q];
+        V[row * l + p] = c * vp - s * vq;
+        V[row * l + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < l * l; e += nt) Vout[e] = V[e];
+  for (int i = tid; i < l; i += nt) lam[i] = A[i * l + i];
+}
+
+cudaError_t jacobi_evd(const double* A, int l, double* V, double* lam, cudaStream_t st) {
+  if (l < 1 || l > 96) return cudaErrorInvalidValue;
+  const int L = (l + 1) & ~1;
+  const size_t smem = (size_t)2 * l * l * 8 + (size_t)L * 8 + (size_t)L * 4 + 16;
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  jacobi_kernel<<<1, 512, smem, st>>>(A, l, V, lam);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void svqb_kernel(const double* V, const double* lam, int l, double tol, float* B) {
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < l; ++i) m = fmax(m, lam[i]);
+    mx = m;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int j = e % l;
+    const double s = lam[j];
+    B[e] = (s > tol * mx && s > 0.0) ? (float)(V[e] / sqrt(s)) : 0.f;
+  }
+}
+
+cudaError_t svqb_matrix(const double* V, const double* lam, int l, double tol, float* B,
+                        cudaStream_t st) {
+  svqb_kernel<<<1, 256, 0, st>>>(V, lam, l, tol, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void to_float_scaled_kernel(const double* C, int la, int lb, const double* lam, float* out) {
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < la * lb; e += blockDim.x * gridDim.x) {
+    const int i = e / lb;
+    out[e] = (float)(lam ? lam[i] * C[e] : C[e]);
+  }
+}
+
+cudaError_t to_float_scaled(const double* C, int la, int lb, const double* lam, float* out,
+                            cudaStream_t st) {
+  to_float_scaled_kernel<<<(la * lb + 255) / 256, 256, 0, st>>>(C, la, lb, lam, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace symnmf

@@ -20,3 +20,11 @@ def cuda_dev():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def S(cuda_dev):
+    # the CUDA library must load on a GPU run: a missing build is an error, not a skip
+    import paper_2402_08134_gb300 as lib
+
+    return lib

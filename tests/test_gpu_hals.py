@@ -1,0 +1,120 @@
+"""GPU parity of the full-X solver (HALS and BPP) with the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import philox
+from oracle import symnmf as O
+from synth import planted_dense, uniform_factor
+
+from ._gpu_util import np64, rel_err, t32, t64
+
+pytestmark = pytest.mark.gpu
+
+
+def _planted(n=1000, k=10, sigma=0.01, seed=0):
+    X, H0, labels = planted_dense(n=n, k=k, sigma=sigma, seed=seed)
+    Hi = uniform_factor(n, k, seed=seed) * O.init_scale(X, k)
+    return X, Hi, labels
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_planted_fp64_hals_100_sweeps(S, use_graph):
+    # planted dense X (n=1000, k=10, FP64), regularised HALS, alpha = max(X), 100 sweeps
+    X, Hi, _ = _planted()
+    s = S.Solver(t64(X), 10, use_graph=use_graph)
+    alpha, nx2 = s.info()
+    assert alpha == pytest.approx(O.default_alpha(X), rel=1e-15)
+    assert nx2 == pytest.approx((X * X).sum(), rel=1e-12)
+    s.set_factors(t32(Hi))
+    got = s.sweep(100)
+    _, _, ref = O.hals_symnmf(X, Hi.astype(np.float32).astype(np.float64), alpha, 100)
+    assert rel_err(got, ref).max() < 1e-4
+    # monotone up to the FP32 rounding of the trace-trick terms (|terms| ~ ||X||^2)
+    assert (np.diff(got) <= 1e-7 * nx2).all()
+
+
+def test_planted_fp32_hals_and_residual(S):
+    X, Hi, labels = _planted(n=1000, k=10, seed=1)
+    s = S.Solver(t32(X), 10)
+    s.set_factors(t32(Hi))
+    got = s.sweep(60)
+    alpha = O.default_alpha(X)
+    W, H, ref = O.hals_symnmf(X, Hi.astype(np.float32).astype(np.float64), alpha, 60)
+    assert rel_err(got, ref).max() < 1e-4
+    nr, obj, pg = s.residual(S.SRC_X, proj_grad=True)
+    Hg, Wg = s.factors()
+    Hg, Wg = np64(Hg), np64(Wg)
+    assert nr == pytest.approx(O.normalized_residual(X, Wg, Hg), rel=1e-4)
+    assert obj == pytest.approx(O.surrogate_objective(X, Wg, Hg, alpha), rel=1e-4)
+    assert pg == pytest.approx(O.projected_gradient_norm(X, Wg, Hg, alpha), rel=1e-3, abs=1e-6)
+    np.testing.assert_allclose(Hg, H, rtol=1e-2, atol=1e-4)
+
+
+def test_bpp_rule_matches_oracle(S):
+    X, Hi, _ = _planted(n=600, k=8, seed=2)
+    s = S.Solver(t64(X), 8)
+    s.set_factors(t32(Hi))
+    got = s.sweep(15, rule=S.RULE_BPP)
+    alpha = O.default_alpha(X)
+    _, _, ref = O.hals_symnmf(X, Hi.astype(np.float32).astype(np.float64), alpha, 15, rule="bpp")
+    assert rel_err(got, ref).max() < 1e-4
+    assert (np.diff(got) <= 1e-7 * (X * X).sum()).all()
+
+
+def test_bpp_rows_equal_exact_nls_from_same_products(S):
+    # one BPP half-step from the GPU's own Y and G equals the oracle's exact NLS of them
+    X, Hi, _ = _planted(n=300, k=12, seed=3)
+    s = S.Solver(t64(X), 12, use_graph=False)
+    s.set_factors(t32(Hi))
+    s.sweep(1, rule=S.RULE_BPP)
+    Hg, Wg = (np64(t) for t in s.factors())
+    H0 = Hi.astype(np.float32).astype(np.float64)
+    alpha = O.default_alpha(X)
+    Wref = O.bpp_update(H0, H0.T @ H0, X @ H0, alpha)
+    np.testing.assert_allclose(Wg, Wref, rtol=1e-4, atol=1e-6)
+
+
+def test_philox_init_matches_oracle(S):
+    X, _, _ = _planted(n=700, k=9, seed=4)
+    s = S.Solver(t64(X), 9, seed=12345)
+    s.init_random(scaled=True)
+    Hg, Wg = (np64(t) for t in s.factors())
+    ref = philox.philox_uniform_factor(700, 9, 12345) * O.init_scale(X, 9)
+    np.testing.assert_allclose(Hg, ref.astype(np.float32), rtol=1e-6)
+    np.testing.assert_array_equal(Hg, Wg)
+    s.init_random(scaled=False)
+    Hg, _ = (np64(t) for t in s.factors())
+    np.testing.assert_array_equal(Hg, philox.philox_uniform_factor(700, 9, 12345).astype(np.float32))
+
+
+def test_rejects_bad_inputs(S):
+    X, Hi, _ = _planted(n=200, k=4, seed=5)
+    s = S.Solver(t32(X), 4)
+    bad = t32(Hi)
+    bad[3, 1] = -1.0
+    with pytest.raises(S.SymNMFError) as e:
+        s.set_factors(bad)
+    assert e.value.status == S.EINVAL
+    with pytest.raises(S.SymNMFError) as e:
+        s.sweep(2, source=S.SRC_LAI)
+    assert e.value.status == S.ESTATE
+    s20 = S.Solver(t32(X), 20)
+    with pytest.raises(S.SymNMFError) as e:
+        s20.sweep(1, rule=S.RULE_BPP)
+    assert e.value.status == S.EUNSUPPORTED
+
+
+def test_edge_sizes(S):
+    # n = 1 and k = 1 and a ragged n that spans several tiles
+    for n, k in [(1, 1), (5, 3), (129, 1), (1031, 64)]:
+        rng = np.random.default_rng(n)
+        A = rng.random((n, n))
+        X = 0.5 * (A + A.T)
+        Hi = rng.random((n, k)) * O.init_scale(X, k)
+        s = S.Solver(t32(X), k)
+        s.set_factors(t32(Hi))
+        got = s.sweep(3)
+        _, _, ref = O.hals_symnmf(X, Hi.astype(np.float32).astype(np.float64), O.default_alpha(X), 3)
+        assert rel_err(got, ref).max() < 1e-4, (n, k)

@@ -1,0 +1,95 @@
+"""GPU parity of LAI-SymNMF: range finder, Apx-EVD and the LAI sweeps."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import symnmf as O
+from synth import gaussian_sketch, gmm_points, kernel_matrix_numpy, median_pair_distance, planted_dense, uniform_factor
+
+from ._gpu_util import np64, rel_err, t32, t64
+
+pytestmark = pytest.mark.gpu
+
+
+def _gmm_kernel(n, d, c, seed):
+    pts, labels = gmm_points(n, d, c, seed=seed)
+    return kernel_matrix_numpy(pts, median_pair_distance(pts, seed=seed)), labels
+
+
+def test_lai_operator_matches_oracle(S):
+    X, _ = _gmm_kernel(2000, 10, 8, seed=0)
+    l, q, k = 30, 2, 10
+    Om = gaussian_sketch(2000, l, seed=1)
+    s = S.Solver(t32(X), k, max_width=l)
+    s.lai_sketch(l, q, t32(Om))
+    U, lam = s.lai()
+    Ug = np64(U)
+    Uo, lo = O.apx_evd(X, Om, q)
+    F = uniform_factor(2000, k, seed=2)
+    got = Ug @ (lam[:, None] * (Ug.T @ F))
+    ref = O.lai_product(Uo, lo, F)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-4
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(l), atol=2e-5)
+    np.testing.assert_allclose(np.sort(lam), np.sort(lo), rtol=1e-4, atol=1e-5 * np.abs(lo).max())
+
+
+def test_exact_range_capture_rank_deficient(S):
+    # planted X of rank 8 < l = 26: the rank-safe CholeskyQR2 keeps the captured range
+    X, _, _ = planted_dense(n=800, k=8, sigma=0.0, seed=3)
+    s = S.Solver(t64(X), 8, max_width=26)
+    s.lai_sketch(26, 1)
+    U, lam = s.lai()
+    Ug = np64(U)
+    A = Ug @ np.diag(lam) @ Ug.T
+    assert np.linalg.norm(X - A) / np.linalg.norm(X) < 1e-5
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_lai_sweeps_match_oracle(S, use_graph):
+    X, _ = _gmm_kernel(3000, 10, 6, seed=4)
+    k, l, q = 6, 22, 2
+    Om = gaussian_sketch(3000, l, seed=5)
+    Hi = uniform_factor(3000, k, seed=6) * O.init_scale(X, k)
+    s = S.Solver(t32(X), k, max_width=l, use_graph=use_graph)
+    s.lai_sketch(l, q, t32(Om))
+    s.set_factors(t32(Hi))
+    got = s.sweep(100, source=S.SRC_LAI)
+    U, lam = O.apx_evd(X, Om, q)
+    _, _, ref = O.lai_symnmf(U, lam, Hi.astype(np.float32).astype(np.float64), O.default_alpha(X), 100)
+    assert rel_err(got, ref).max() < 1e-4
+
+
+def test_lai_bf16_then_fp32_refinement_reaches_oracle_residual(S):
+    # X stored BF16 for the sketch, FP32 copy for the refinement sweeps (Iterative Refinement)
+    n, k, l, q = 4000, 8, 26, 2
+    X, _ = _gmm_kernel(n, 12, 8, seed=7)
+    Xf = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Xb = Xf.to(torch.bfloat16)
+    Hi = uniform_factor(n, k, seed=8) * O.init_scale(X, k)
+    alpha = O.default_alpha(X)
+    W, H, _ = O.hals_symnmf(X, Hi, alpha, 60, record=False)
+    nr_oracle = O.normalized_residual(X, W, H)
+    s = S.Solver(Xb, k, x_hi=Xf, max_width=l)
+    s.lai_sketch(l, q)
+    s.set_factors(t32(Hi))
+    s.sweep(60, source=S.SRC_LAI, record=False)
+    s.sweep(5, source=S.SRC_XHI, record=False)
+    nr, _ = s.residual(S.SRC_XHI)
+    assert nr <= nr_oracle + 1e-3
+
+
+def test_lai_fp8_sketch_is_close(S):
+    n, k, l = 3000, 8, 26
+    X, _ = _gmm_kernel(n, 12, 8, seed=9)
+    Xf = torch.tensor(X, dtype=torch.float32, device="cuda")
+    x8, rs = S.quantize_fp8(Xf)
+    s = S.Solver(x8, k, row_scale=rs, x_hi=Xf, max_width=l)
+    s.lai_sketch(l, 2)
+    Hi = uniform_factor(n, k, seed=10) * O.init_scale(X, k)
+    s.set_factors(t32(Hi))
+    s.sweep(60, source=S.SRC_LAI, record=False)
+    s.sweep(5, source=S.SRC_XHI, record=False)
+    nr, _ = s.residual(S.SRC_XHI)
+    W, H, _ = O.hals_symnmf(X, Hi, O.default_alpha(X), 60, record=False)
+    assert nr <= O.normalized_residual(X, W, H) + 1e-3
