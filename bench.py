@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the randomized SymNMF hot path on one GB300 (per rank).
+
+Workload (the LAI-SymNMF configuration): n = 20000 points of a 20-component
+Gaussian mixture in R^50, X_ij = exp(-||x_i - x_j||^2 / sigma^2) with sigma
+the median pairwise distance, k = 20, sketch width l = 2k + 10 = 50, q = 2
+power iterations, 200 sweeps, alpha = max(X).  X is generated on the device
+(synthetic data) and stored as BF16 (0.8 GB, larger than L2) for the
+tensor-core products and as FP32 for the plain form and the final check.
+
+One step = one complete solve in the mixed form:
+  Philox start -> range finder with re-orthonormalisation on BF16 X
+  (6 tcgen05 passes over X) -> Apx-EVD -> 200 LAI sweeps (CUDA graph) ->
+  2 refinement sweeps with the full BF16 X -> residual against BF16 X.
+The metric is the step time in seconds (lower is better); after timing, the
+solution's residual against the FP32 X is compared with the FP64 oracle's
+residual after 200 plain sweeps (stored in tests/golden/c2_reference.json):
+it must be within 1e-3.
+
+Also reported: the plain FP32 form (FP32 X, full X.H every sweep, 200 sweeps,
+same start) timed the same way, the end-to-end time through the public API
+with X copied in from pinned host memory, the live roofline of the tcgen05
+product kernel, SM clocks sampled during the timed region, and the oracle
+timed on the host cores.  `--impl reference` times the oracle itself.
+
+Multi-GPU: the method does not shard at these sizes; each rank solves its own
+replica of the workload (independent replicas, weak scaling) and rank 0
+prints the maximum step time over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, D, C, K, L, Q, SWEEPS, SEED = 20000, 50, 20, 20, 50, 2, 200, 1
+N_REFINE = 2
+METRIC = "time to oracle residual (s) & X·H TFLOP/s|GB/s, mixed/batched/learned vs plain FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch sweep kernels one by one instead of replaying recorded graphs (for profilers)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- workload
+
+
+def workload_points():
+    from synth import gmm_points, median_pair_distance
+
+    pts, _ = gmm_points(N, D, C, seed=0)
+    return pts, median_pair_distance(pts, seed=0)
+
+
+def golden():
+    path = os.path.join(ROOT, "tests", "golden", "c2_reference.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the product kernel from the committed ncu summary, if it still matches the source."""
+    path = os.path.join(ROOT, "profiles", "xf_tc_bf16_n20000_traffic.txt")
+    src = os.path.join(ROOT, "paper_2402_08134_gb300", "csrc", "gemm_tc.cu")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            a, b = line.split("=", 1)
+            vals[a.strip()] = b.strip()
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if vals.get("source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------- oracle side
+
+
+def oracle_sample(pts, sigma, sweeps_sample=20):
+    """The FP64 oracle on the same instance: sketch + `sweeps_sample` LAI sweeps, scaled to 200 sweeps."""
+    import numpy as np
+
+    from oracle import philox
+    from oracle import symnmf as O
+    from synth import kernel_matrix_numpy
+
+    X = kernel_matrix_numpy(pts, sigma)
+    alpha = O.default_alpha(X)
+    H0 = philox.philox_uniform_factor(N, K, SEED) * O.init_scale(X, K)
+    Om = philox.philox_gaussian(N, L, SEED)
+
+    def one():
+        t0 = time.perf_counter()
+        U, lam = O.apx_evd(X, Om, Q)
+        t1 = time.perf_counter()
+        O.lai_symnmf(U, lam, H0, alpha, sweeps_sample, record=False)
+        t2 = time.perf_counter()
+        return (t1 - t0) + (t2 - t1) * (SWEEPS / sweeps_sample)
+
+    del np
+    return one
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2402_08134_gb300 as S
+    from synth import kernel_matrix_torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pts, sigma = workload_points()
+    Xf = kernel_matrix_torch(pts, sigma, dev)
+    Xb = Xf.to(torch.bfloat16)
+    torch.cuda.synchronize()
+
+    s = S.Solver(Xb, K, max_width=L, seed=SEED, x_hi=Xf, use_graph=not args.no_graph)
+
+    def step():
+        s.init_random(True)
+        s.lai_sketch(L, Q)
+        s.sweep(SWEEPS, source=S.SRC_LAI, record=False)
+        s.sweep(N_REFINE, source=S.SRC_X, record=False)
+        return s.residual(S.SRC_X)[0]
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = S.launch_count()
+    s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    prod_ms, prod_n, prod_bytes = s.profile_read()
+    s.profile(False)
+    launches = S.launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # verification against the oracle's residual (untimed)
+    nr_true = s.residual(S.SRC_XHI)[0]
+    gold = golden()
+    target = (gold["plain_nr"] + 1e-3) if gold else None
+
+    out = {}
+    # plain FP32 comparator: same start, FP32 X, full X.H every sweep
+    if not args.no_plain:
+        sp = S.Solver(Xf, K, seed=SEED, use_graph=not args.no_graph)
+        sp.init_random(True)
+        sp.sweep(1, record=False)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sp.init_random(True)
+        sp.sweep(SWEEPS, source=S.SRC_X, record=False)
+        nr_plain = sp.residual(S.SRC_X)[0]
+        b.record(stream)
+        torch.cuda.synchronize()
+        out["plain_fp32"] = {"s": a.elapsed_time(b) / 1e3, "nr": nr_plain,
+                             "ok_vs_oracle": (abs(nr_plain - gold["plain_nr"]) <= 1e-4 * gold["plain_nr"])
+                             if gold else None}
+        sp.close()
+
+    # end to end through the public API: X from pinned host memory, result back to host
+    Xh = Xb.cpu().pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        Xd = Xh.to(dev, non_blocking=True)
+        se = S.Solver(Xd, K, max_width=L, seed=SEED, use_graph=not args.no_graph)
+        se.init_random(True)
+        se.lai_sketch(L, Q)
+        se.sweep(SWEEPS, source=S.SRC_LAI, record=False)
+        se.sweep(N_REFINE, source=S.SRC_X, record=False)
+        nr = se.residual(S.SRC_X)[0]
+        H, _ = se.factors()
+        Hh = H.cpu()
+        se.close()
+        return nr, Hh
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = a.elapsed_time(b) / 1e3 / e2e_steps
+
+    pk, pk_kind = peaks()
+    avg_launch_ms = prod_ms / max(prod_n, 1)
+    bytes_per_launch = prod_bytes / max(prod_n, 1)
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if prod_n else None
+    roof = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F, N=l=50)", "bound": "hbm", "achieved": achieved,
+            "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
+            "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": recorded_traffic(),
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "launches": prod_n,
+            "tflops": (2.0 * N * N * L / (avg_launch_ms * 1e-3) / 1e12) if prod_n else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        one = oracle_sample(pts, sigma)
+        t = one()
+        cpu = {"value": t, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "FP64 oracle on the same instance: Apx-EVD (q=2, l=50) + 20 of the 200 LAI sweeps, "
+                         "sweep time scaled x10; X built in FP64 beforehand (untimed)"}
+
+    value = ms_step / 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (Gaussian-mixture kernel matrix generated on the device)",
+        "config": {"workload": "LAI-SymNMF, dense Gaussian-kernel X n=20000 (20-component GMM in R^50), "
+                               "k=20, l=50, q=2, 200 sweeps + 2 full-X refinement sweeps, X in BF16",
+                   "n": N, "k": K, "l": L, "q": Q, "sweeps": SWEEPS, "refine_sweeps": N_REFINE,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (BF16 X = 0.8 GB)"},
+        "nr_true": nr_true, "nr_target": target, "reached_target": (nr_true <= target) if target else None,
+        "forms": out,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Xh.numel() * 2),
+                "d2h_bytes_per_step": int(N * K * 4)},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    del np
+
+
+# ------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    pts, sigma = workload_points()
+    one = oracle_sample(pts, sigma)
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
+    v = sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "LAI-SymNMF, dense Gaussian-kernel X n=20000 (20-component GMM in R^50), "
+                               "k=20, l=50, q=2, 200 sweeps", "n": N, "k": K, "l": L, "q": Q, "sweeps": SWEEPS},
+        "cpu_baseline": {"value": v, "unit": "s", "kind": "oracle", "cores": os.cpu_count(),
+                         "sample": "per step: Apx-EVD + 20 LAI sweeps on the full instance, sweeps scaled x10"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

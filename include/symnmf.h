@@ -104,7 +104,9 @@ typedef struct {
   int32_t use_graph;  /* 1: record sweep bodies as CUDA graphs once and replay them */
   int32_t max_width;  /* largest sketch width l to be requested (0: 2k + 10); <= 128 */
   int32_t max_samples;/* largest sample count s for LvS calls (0: n) */
-  int32_t reserved[4];
+  int32_t lai_mode;   /* LAI-HALS sweeps: 0 = one persistent cooperative launch for
+                         all sweeps (default), 1 = separate kernels per step */
+  int32_t reserved[3];
 } symnmf_options;
 
 /* ------------------------------------------------------------------ handle */
@@ -134,12 +136,16 @@ symnmf_status symnmf_get_factors(symnmf_t h, float* H_out, float* W_out);
 
 /* Alg. RRF + Alg. Apx-EVD: Y = X Omega, Q = orth(Y), q times
  * { Q = orth(X Q); Q = orth(X Q) }, T = Q^T X Q, T = V Lambda V^T,
- * U = Q V.  orth() is a rank-safe CholeskyQR2 (first pass through the
- * eigen-decomposition of Y^T Y, second pass Cholesky), FP64 on the l x l
- * factors.  `omega` (device n x l float32) or NULL for the Philox Gaussian
+ * U = Q V.  orth() is a rank-safe shifted CholeskyQR3 (Fukaya et al. 2020):
+ * Grams accumulated in FP64, Cholesky in FP64, pivots below 1e-10 of the
+ * largest dropped; the l x l eigen-decomposition is a cyclic Jacobi in FP64.  `omega` (device n x l float32) or NULL for the Philox Gaussian
  * stream (counter (p, i lo, i hi, 1)).  l in [k, max_width], q >= 0.
  * X passes use the problem's X (BF16/FP8 on tensor cores when so stored). */
 symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega);
+/* Use a given low-rank approximation X ~ U Lambda U^T instead of a sketch
+ * (U device n x l float32 with orthonormal columns, Lambda host double[l]),
+ * e.g. a truncated EVD computed elsewhere.  Copies both; synchronises. */
+symnmf_status symnmf_set_lai(symnmf_t h, const float* U, const double* lam_host, int l);
 /* U (device n x l float32, may be NULL) and Lambda (host double[l], may be NULL). */
 symnmf_status symnmf_get_lai(symnmf_t h, float* U_out, double* lam_out, int* l_out);
 
@@ -214,6 +220,14 @@ symnmf_status symnmf_quantize_fp8(const float* x, int64_t n, int64_t ldx, uint8_
 /* BF16 copy of a dense float X (round to nearest even). */
 symnmf_status symnmf_convert_bf16(const float* x, int64_t n, int64_t ldx, uint16_t* xb, int64_t ldb,
                                   void* stream);
+
+/* Live timing of the dense tensor-core product kernel.  While enabled, every
+ * eager (not graph-recorded) product launch on the handle is bracketed by
+ * CUDA events on the handle's stream.  profile_read synchronises and returns
+ * the summed kernel time (ms), the number of launches and their algorithmic
+ * bytes (X once, F and Y once each), then resets the record. */
+symnmf_status symnmf_profile(symnmf_t h, int enable);
+symnmf_status symnmf_profile_read(symnmf_t h, double* total_ms, int64_t* launches, double* bytes);
 
 /* Number of kernels this library has launched in this process (graph replays
  * count each kernel node). */

@@ -56,7 +56,7 @@ class symnmf_problem(C.Structure):
 
 class symnmf_options(C.Structure):
     _fields_ = [("gemm", C.c_int32), ("use_graph", C.c_int32), ("max_width", C.c_int32),
-                ("max_samples", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("max_samples", C.c_int32), ("lai_mode", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _P = C.c_void_p
@@ -76,6 +76,7 @@ _SIGS = {
     "symnmf_get_factors": (_I, [_P, _P, _P]),
     "symnmf_lai_sketch": (_I, [_P, _I, _I, _P]),
     "symnmf_get_lai": (_I, [_P, _P, _DP, _IP]),
+    "symnmf_set_lai": (_I, [_P, _P, _DP, _I]),
     "symnmf_hals_sweep": (_I, [_P, _I, _I, _I, _DP]),
     "symnmf_leverage": (_I, [_P, _I, _P]),
     "symnmf_lvs_sample": (_I, [_P, _I, _I, _D, _I, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_float), _I,
@@ -90,6 +91,8 @@ _SIGS = {
     "symnmf_quantize_fp8": (_I, [_P, _I64, _I64, _P, _I64, _P, _P]),
     "symnmf_convert_bf16": (_I, [_P, _I64, _I64, _P, _I64, _P]),
     "symnmf_launch_count": (C.c_uint64, []),
+    "symnmf_profile": (_I, [_P, _I]),
+    "symnmf_profile_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
     "symnmf_batched_create": (_I, [C.POINTER(symnmf_problem), _I, _I, C.POINTER(symnmf_options), _P,
                                    C.POINTER(_P)]),
     "symnmf_batched_destroy": (None, [_P]),
@@ -160,7 +163,7 @@ class Solver:
     """
 
     def __init__(self, X=None, k=10, *, csr=None, n=None, row_scale=None, x_hi=None, alpha=0.0, seed=0,
-                 gemm=GEMM_AUTO, use_graph=True, max_width=0, max_samples=0, stream=None):
+                 gemm=GEMM_AUTO, use_graph=True, max_width=0, max_samples=0, lai_mode=0, stream=None):
         import torch
 
         self._keep = [X, csr, row_scale, x_hi]
@@ -194,6 +197,7 @@ class Solver:
         o.use_graph = 1 if use_graph else 0
         o.max_width = max_width
         o.max_samples = max_samples
+        o.lai_mode = lai_mode
         self.n, self.k = int(p.n), int(k)
         self.stream = stream
         h = C.c_void_p()
@@ -239,6 +243,12 @@ class Solver:
     # -- LAI
     def lai_sketch(self, l, q, omega=None):
         self._chk(symnmf_lai_sketch(self.h, l, q, _ptr(omega)))
+
+    def set_lai(self, U, lam):
+        import numpy as np
+
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._chk(symnmf_set_lai(self.h, _ptr(U), lam.ctypes.data_as(_DP), int(lam.shape[0])))
 
     def lai(self):
         import numpy as np
@@ -300,6 +310,15 @@ class Solver:
 
     def lvs_iterate(self, iters, tau, s, rule=RULE_HALS, iter0=0):
         self._chk(symnmf_lvs_iterate(self.h, iter0, iters, tau, s, rule))
+
+    # -- live kernel timing
+    def profile(self, enable=True):
+        self._chk(symnmf_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        t, n, b = C.c_double(), C.c_int64(), C.c_double()
+        self._chk(symnmf_profile_read(self.h, C.byref(t), C.byref(n), C.byref(b)))
+        return t.value, n.value, b.value
 
     # -- residual
     def residual(self, source=SRC_X, proj_grad=False):
@@ -373,6 +392,75 @@ class Batch:
         a, b, t = C.c_int(), C.c_int(), C.c_double()
         self._chk(symnmf_batched_info(self.h, C.byref(a), C.byref(b), C.byref(t)))
         return dict(stages=a.value, ctas_per_sm=b.value, product_ms=t.value)
+
+
+class MLP:
+    """Warm-start network (wraps symnmf_mlp_*): rows of normalised X Omega -> H0 rows."""
+
+    def __init__(self, dims=(74, 256, 256, 32), seed=0, stream=None):
+        h = C.c_void_p()
+        st = symnmf_mlp_create(dims[0], dims[1], dims[2], dims[3], seed, _stream(stream), C.byref(h))
+        if st != OK:
+            raise SymNMFError(st, "symnmf_mlp_create")
+        self.h, self.dims = h, tuple(dims)
+        self.count = int(symnmf_mlp_param_count(h))
+        self.t = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            symnmf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+
+        out = np.zeros(self.count, dtype=np.float32)
+        check(symnmf_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p), self.count))
+        return out
+
+    def set_params(self, flat):
+        import numpy as np
+
+        arr = np.ascontiguousarray(flat, dtype=np.float32)
+        check(symnmf_mlp_set_params(self.h, arr.ctypes.data_as(C.c_void_p), self.count))
+
+    def unflatten(self, flat):
+        d = self.dims
+        out, o = [], 0
+        for a, b in zip(d[:-1], d[1:]):
+            out.append(flat[o:o + a * b].reshape(a, b))
+            o += a * b
+            out.append(flat[o:o + b])
+            o += b
+        return out
+
+    def forward(self, x):
+        import torch
+
+        out = torch.empty((x.shape[0], self.dims[3]), dtype=torch.float32, device=x.device)
+        check(symnmf_mlp_forward(self.h, _ptr(x), x.shape[0], _ptr(out)))
+        return out
+
+    def loss_grad(self, x, Hstar, want_grads=False):
+        import torch
+
+        g = torch.empty(self.count, dtype=torch.float32, device=x.device) if want_grads else None
+        loss = C.c_double()
+        check(symnmf_mlp_loss_grad(self.h, _ptr(x), _ptr(Hstar), x.shape[0], _ptr(g), C.byref(loss)))
+        return (loss.value, g) if want_grads else loss.value
+
+    def adam(self, lr=1e-3):
+        self.t += 1
+        check(symnmf_mlp_adam(self.h, C.c_float(lr), self.t))
+
+    def warm_start(self, solver, features=None):
+        check(symnmf_warm_start(solver.h, self.h, _ptr(features)), solver.h)
 
 
 def dense_xf(X, F, *, row_scale=None, gemm=GEMM_AUTO, N=None, stream=None):

@@ -566,6 +566,7 @@ struct symnmf_batch_ctx {
   size_t partial_floats = 0;
   // tuned product configuration
   int stages = 6, ctas_per_sm = 1, G = 0, max_segs = 1;
+  size_t hals_smem = 0;  // dynamic shared memory of the grouped HALS kernel
   bool tuned = false;
   double tuned_ms = 0.0;
   cudaGraphExec_t graph = nullptr;
@@ -682,7 +683,7 @@ static symnmf_status batched_half(symnmf_batch_t b, int side) {
   const int gfix = side ? 1 : 0, gupd = side ? 0 : 1;
   BTRYS(batched_product(b, Ff));
   BTRY(cudaMemsetAsync(b->part, 0, (size_t)2 * b->PR * sizeof(double), b->st));
-  grouped_hals_kernel<32><<<(unsigned)b->hals_tiles, GH_ROWS, 0, b->st>>>(
+  grouped_hals_kernel<32><<<(unsigned)b->hals_tiles, GH_ROWS, b->hals_smem, b->st>>>(
       b->d_hp, b->d_tile_off, b->nprob, Fu, Ff, b->Y, b->Gd[gfix], b->part, b->err);
   count_launches(1);
   BTRY(cudaGetLastError());
@@ -835,6 +836,15 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
     b->hp.push_back(h);
   }
   row_off[nprob] = rows;
+  // grouped HALS: R k x k Grams, R k inverses, Y / H / W tiles of 64 padded rows
+  for (int p = 0; p < nprob; ++p) {
+    const int k = probs[p].k, RW = restarts * k;
+    const size_t need = (size_t)(restarts * k * k + restarts * k + 3 * GH_ROWS * (RW + 1)) * sizeof(float);
+    b->hals_smem = std::max(b->hals_smem, need);
+  }
+  if (cudaFuncSetAttribute(grouped_hals_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)b->hals_smem) != cudaSuccess)
+    return bail(SYMNMF_ECUDA);
   b->PR = pr;
   b->total_f = f;
   b->total_g = g;

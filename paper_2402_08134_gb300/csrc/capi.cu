@@ -143,8 +143,23 @@ symnmf_status product(symnmf_t h, int src, const float* F, int N, int ldf, float
         TRY(pack_ft_bf16(F, h->n, ldf, N, BN, h->fpack, h->ldp, h->st));
       else
         TRY(pack_ft_fp8(F, h->n, ldf, N, BN, h->fpack, h->ldp, h->colscale, h->st));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (h->profiling && !h->capturing) {
+        if (h->prof_used == h->prof_events.size()) {
+          cudaEvent_t a, b;
+          TRY(cudaEventCreate(&a));
+          TRY(cudaEventCreate(&b));
+          h->prof_events.push_back({a, b});
+          h->prof_bytes.push_back(0.0);
+        }
+        e0 = h->prof_events[h->prof_used].first;
+        e1 = h->prof_events[h->prof_used].second;
+        const double es = fmt == SYMNMF_X_DENSE_BF16 ? 2.0 : 1.0;
+        h->prof_bytes[h->prof_used] = (double)h->n * h->n * es + (double)h->n * N * (es + 4.0);
+        h->prof_used++;
+      }
       TRY(xf_tc(fmt, h->p.x, h->ldx, h->p.row_scale, h->n, h->fpack, h->ldp, h->colscale, N, Y, ldy,
-                h->gemm_ws, h->gemm_ws_floats, h->err, h->st));
+                h->gemm_ws, h->gemm_ws_floats, h->err, h->st, e0, e1));
       return SYMNMF_OK;
     }
     case SYMNMF_X_CSR_F32:
@@ -320,6 +335,10 @@ extern "C" void symnmf_destroy(symnmf_t h) {
   for (auto& g : h->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  for (auto& pr : h->prof_events) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -388,6 +407,10 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
   TRY(dalloc(h, &h->ev, (size_t)L));
   TRY(dalloc(h, &h->Sm_f, (size_t)L * L));
   TRY(dalloc(h, &h->Rl_f, (size_t)L * L));
+  TRY(dalloc(h, &h->eng_part, lai_engine_part_doubles(L, h->k)));
+  TRY(dalloc(h, &h->eng_fin, lai_engine_fin_doubles(L, h->k)));
+  TRY(dalloc(h, &h->eng_G, (size_t)2 * h->k * h->k));
+  TRY(dalloc(h, &h->eng_bar, 2));
   h->lai_cap = L;
   TRYS(ensure_gemm_ws(h, L));
   return SYMNMF_OK;
@@ -447,6 +470,20 @@ extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float
   TRY(to_float_scaled(h->V_d, l, l, nullptr, h->Sm_f, h->st));
   TRY(apply_small(A, l, l, h->Sm_f, l, n, h->U, l, h->st));
   TRY(sumsq(h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  h->l = l;
+  h->lai_ready = true;
+  h->lai_version++;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_set_lai(symnmf_t h, const float* U, const double* lam_host, int l) {
+  if (!h || !U || !lam_host) return SYMNMF_EINVAL;
+  if (l < h->k || l > h->o.max_width) return fail(h, SYMNMF_EINVAL, "need k <= l <= max_width");
+  TRYS(ensure_lai(h, l));
+  TRY(cudaMemcpyAsync(h->U, U, (size_t)h->n * l * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  TRY(cudaMemcpyAsync(h->lam, lam_host, (size_t)l * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  TRY(sumsq(h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  TRY(cudaStreamSynchronize(h->st));  // lam_host may be released on return
   h->l = l;
   h->lai_ready = true;
   h->lai_version++;
@@ -537,9 +574,36 @@ static symnmf_status get_graph(symnmf_t h, int src, int rule, symnmf_ctx::Graph*
   return SYMNMF_OK;
 }
 
+// LAI-HALS sweeps in one cooperative launch per chunk of sweeps.
+static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host) {
+  const int k = h->k;
+  int done = 0;
+  while (done < nsweeps) {
+    const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
+    TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_part,
+                   h->eng_fin, h->obj_ring, OBJ_RING, h->eng_G, h->eng_bar, h->err, h->st));
+    if (obj_host) {
+      TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->st));
+      TRYS(check_device_error(h));
+    }
+    done += chunk;
+  }
+  if (nsweeps > 0) {
+    // the handle's Grams follow the engine's final factors
+    TRY(cudaMemcpyAsync(h->Gd[0], h->eng_G, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+    TRY(cudaMemcpyAsync(h->Gd[1], h->eng_G + k * k, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+    TRY(to_float_scaled(h->Gd[0], k, k, nullptr, h->Gf[0], h->st));
+    TRY(to_float_scaled(h->Gd[1], k, k, nullptr, h->Gf[1], h->st));
+  }
+  return SYMNMF_OK;
+}
+
 extern "C" symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, double* obj_host) {
   if (!h || nsweeps < 0) return SYMNMF_EINVAL;
   TRYS(validate_sweep(h, source, rule));
+  if (source == SYMNMF_SRC_LAI && rule == SYMNMF_RULE_HALS && h->o.lai_mode == 0)
+    return lai_engine_sweeps(h, nsweeps, obj_host);
   int done = 0;
   bool warmed = false;
   while (done < nsweeps) {
@@ -833,4 +897,30 @@ extern "C" symnmf_status symnmf_convert_bf16(const float* x, int64_t n, int64_t 
                                              void* stream) {
   if (!x || !xb || n < 1 || ldx < n || ldb < n) return SYMNMF_EINVAL;
   return to_status(convert_bf16(x, n, ldx, xb, ldb, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------- profiling
+
+extern "C" symnmf_status symnmf_profile(symnmf_t h, int enable) {
+  if (!h) return SYMNMF_EINVAL;
+  h->profiling = enable != 0;
+  h->prof_used = 0;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_profile_read(symnmf_t h, double* total_ms, int64_t* launches, double* bytes) {
+  if (!h) return SYMNMF_EINVAL;
+  TRY(cudaStreamSynchronize(h->st));
+  double t = 0.0, by = 0.0;
+  for (size_t i = 0; i < h->prof_used; ++i) {
+    float ms = 0.f;
+    TRY(cudaEventElapsedTime(&ms, h->prof_events[i].first, h->prof_events[i].second));
+    t += ms;
+    by += h->prof_bytes[i];
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = (int64_t)h->prof_used;
+  if (bytes) *bytes = by;
+  h->prof_used = 0;
+  return SYMNMF_OK;
 }

@@ -379,7 +379,8 @@ static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const
 
 cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, int64_t n,
                   const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y, int ldy,
-                  float* ws, size_t ws_floats, unsigned* err, cudaStream_t st) {
+                  float* ws, size_t ws_floats, unsigned* err, cudaStream_t st, cudaEvent_t ev_begin,
+                  cudaEvent_t ev_end) {
   const bool fp8 = fmt == 3;
   if (!fp8 && fmt != 2) return cudaErrorInvalidValue;
   const int BN = tc_block_n(N);
@@ -397,6 +398,7 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel, (uint32_t)BN))
     return cudaErrorInvalidValue;
   cudaError_t e;
+  if (ev_begin) cudaEventRecord(ev_begin, st);
   if (fp8) {
     switch (BN) {
       case 32: e = launch_tc<32, true>(ma, mb, p, ws, err, st); break;
@@ -412,6 +414,7 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
       default: e = launch_tc<256, false>(ma, mb, p, ws, err, st); break;
     }
   }
+  if (ev_end) cudaEventRecord(ev_end, st);
   if (e != cudaSuccess) return e;
   const int64_t work = n * N;
   tc_reduce_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(

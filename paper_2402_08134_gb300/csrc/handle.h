@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/symnmf.h"
@@ -68,6 +69,8 @@ struct symnmf_ctx {
   float *Om = nullptr, *Qa = nullptr, *Qb = nullptr, *U = nullptr, *Mf = nullptr;
   double *Sm_d = nullptr, *V_d = nullptr, *lam = nullptr, *ev = nullptr;
   float *Sm_f = nullptr, *Rl_f = nullptr;
+  double *eng_part = nullptr, *eng_fin = nullptr, *eng_G = nullptr;  // LAI engine buffers
+  unsigned* eng_bar = nullptr;
 
   // LvS
   symnmf::SampleBufs sb{};
@@ -83,4 +86,10 @@ struct symnmf_ctx {
   } graphs[6];
   bool capturing = false;
   cudaStream_t cap_st = nullptr;
+
+  // live timing of the tensor-core product kernel (eager calls only)
+  bool profiling = false;
+  size_t prof_used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  std::vector<double> prof_bytes;
 };

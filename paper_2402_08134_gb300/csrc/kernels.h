@@ -33,7 +33,8 @@ cudaError_t pack_ft_fp8(const float* F, int64_t n, int ldf, int N, int Npad, voi
                         float* col_scale, cudaStream_t st);
 cudaError_t xf_tc(int fmt /*BF16 or FP8*/, const void* X, int64_t ldx, const float* row_scale,
                   int64_t n, const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y,
-                  int ldy, float* ws, size_t ws_floats, unsigned* err, cudaStream_t st);
+                  int ldy, float* ws, size_t ws_floats, unsigned* err, cudaStream_t st,
+                  cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 // ------------------------------------------------------------------ sparse
 cudaError_t csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
@@ -141,6 +142,14 @@ struct SampleBufs {
 int sampler_blocks(int64_t n);
 cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, uint64_t seed,
                           uint32_t iter, uint32_t side, cudaStream_t st);
+
+// ------------------------------------------------------------- LAI engine
+// All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu).
+size_t lai_engine_part_doubles(int l, int k);
+size_t lai_engine_fin_doubles(int l, int k);
+cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
+                       int nsweeps, double alpha, const double* normX2, double* part, double* fin, double* obj,
+                       int obj_cap, double* Gout, unsigned* bar, unsigned* err, cudaStream_t st);
 
 // -------------------------------------------------------------------- BPP
 cudaError_t bpp_rows(float* F_upd, const float* F_fix, int64_t n, int k, const double* G,

@@ -145,6 +145,7 @@ cudaError_t xstats(int fmt, const void* x, int64_t ldx, const float* row_scale, 
 
 constexpr int XC_THREADS = 256;
 constexpr int XC_CHUNK = 32;
+constexpr int XC_FOLD = 8;  // chunks summed (compensated FP32) before the FP64 accumulation
 
 size_t xcross_ws_doubles(int la, int lb) { return (size_t)2 * num_sms() * la * lb + 64; }
 
@@ -174,34 +175,33 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = min(count, r0 + per);
 
+  // FP32 partial sums carry a Kahan compensation term (fc), so their error
+  // stays O(eps) however many rows they cover; they are folded into FP64
+  // every XC_FOLD chunks.  The trace-trick objective cancels terms of size
+  // ||X||^2, so the Grams need this accuracy.
   double acc[TPT][16];
+  float f[TPT][16], fc[TPT][16];
 #pragma unroll
   for (int t = 0; t < TPT; ++t)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[t][e] = 0.0;
+    for (int e = 0; e < 16; ++e) acc[t][e] = 0.0, f[t][e] = 0.f, fc[t][e] = 0.f;
 
-  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK) {
-    // stage the chunk
-    for (int e = tid; e < XC_CHUNK * la4; e += XC_THREADS) {
-      const int rr = e / la4, c = e - rr * la4;
+  // a Gram (same operand, no weights) stages its rows once
+  const bool same = (A == B) && (lda == ldb) && (la == lb) && !wt;
+  const float* Bsrc = same ? As : Bs;
+  const int lane = tid & 31, wid = tid >> 5;
+  int chunk_no = 0;
+  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK, ++chunk_no) {
+    // stage the chunk: one warp per row, lanes along the row (coalesced)
+    for (int rr = wid; rr < XC_CHUNK; rr += XC_THREADS / 32) {
       const int64_t r = rb + rr;
-      float v = 0.f;
-      if (r < r1 && c < la) {
-        const int64_t src = idx ? (int64_t)idx[r] : r;
-        v = A[src * lda + c];
+      const bool live = r < r1;
+      const int64_t src = live ? (idx ? (int64_t)idx[r] : r) : 0;
+      for (int c = lane; c < la4; c += 32) As[rr * la4 + c] = (live && c < la) ? A[src * lda + c] : 0.f;
+      if (!same) {
+        const float w = (live && wt) ? wt[r] : 1.f;
+        for (int c = lane; c < lb4; c += 32) Bs[rr * lb4 + c] = (live && c < lb) ? B[src * ldb + c] * w : 0.f;
       }
-      As[e] = v;
-    }
-    for (int e = tid; e < XC_CHUNK * lb4; e += XC_THREADS) {
-      const int rr = e / lb4, c = e - rr * lb4;
-      const int64_t r = rb + rr;
-      float v = 0.f;
-      if (r < r1 && c < lb) {
-        const int64_t src = idx ? (int64_t)idx[r] : r;
-        v = B[src * ldb + c];
-        if (wt) v *= wt[r];
-      }
-      Bs[e] = v;
     }
     __syncthreads();
     if (active) {
@@ -210,22 +210,34 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
         const int tile = (T >= XC_THREADS) ? tid + t * XC_THREADS : tid % T;
         if (tile < T) {
           const int ti = tile / tb, tj = tile - ti * tb;
-          float f[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) f[e] = 0.f;
           for (int rr = rg; rr < XC_CHUNK; rr += R) {
             const float4 a = *(const float4*)(As + rr * la4 + 4 * ti);
-            const float4 b = *(const float4*)(Bs + rr * lb4 + 4 * tj);
+            const float4 b = *(const float4*)(Bsrc + rr * lb4 + 4 * tj);
             const float av[4] = {a.x, a.y, a.z, a.w};
             const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) f[p * 4 + q] = fmaf(av[p], bv[q], f[p * 4 + q]);
+              for (int q = 0; q < 4; ++q) {
+                // Kahan step: y = a b - c; t = s + y; c = (t - s) - y; s = t
+                const float y = fmaf(av[p], bv[q], -fc[t][p * 4 + q]);
+                const float s2 = f[t][p * 4 + q] + y;
+                fc[t][p * 4 + q] = (s2 - f[t][p * 4 + q]) - y;
+                f[t][p * 4 + q] = s2;
+              }
           }
-#pragma unroll
-          for (int e = 0; e < 16; ++e) acc[t][e] += (double)f[e];
         }
+      }
+      // compensated FP32 over XC_FOLD chunks, then FP64
+      if ((chunk_no % XC_FOLD) == XC_FOLD - 1 || rb + XC_CHUNK >= r1) {
+#pragma unroll
+        for (int t = 0; t < TPT; ++t)
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            acc[t][e] += (double)f[t][e] - (double)fc[t][e];
+            f[t][e] = 0.f;
+            fc[t][e] = 0.f;
+          }
       }
     }
     __syncthreads();
@@ -359,45 +371,59 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
     const int64_t base = tile * HALS_ROWS;
     const int rows = (int)min((int64_t)HALS_ROWS, n - base);
     // coalesced staging of the tile's rows
-    for (int e = tid; e < rows * RW; e += HALS_ROWS) {
-      const int rr = e / RW, c = e - rr * RW;
-      Hs[rr * P + c] = Ff[(base + rr) * RW + c];
-      Ws[rr * P + c] = Fu[(base + rr) * RW + c];
-      if (!U) Ys[rr * P + c] = Y[(base + rr) * (int64_t)ldy + c];
-    }
-    if (U)
-      for (int e = tid; e < rows * l; e += HALS_ROWS) {
-        const int rr = e / l, c = e - rr * l;
-        Us[rr * (l + 1) + c] = U[(base + rr) * (int64_t)l + c];
+    // coalesced staging, one warp per row (no index division)
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int rr = wid; rr < rows; rr += HALS_ROWS / 32) {
+      const int64_t g = (base + rr);
+      for (int c = lane; c < RW; c += 32) {
+        Hs[rr * P + c] = Ff[g * RW + c];
+        Ws[rr * P + c] = Fu[g * RW + c];
+        if (!U) Ys[rr * P + c] = Y[g * (int64_t)ldy + c];
       }
+      if (U)
+        for (int c = lane; c < l; c += 32) Us[rr * (l + 1) + c] = U[g * (int64_t)l + c];
+    }
     __syncthreads();
     if (tid < rows) {
-      float* yr = Ys + tid * P;
+      const float* yr = Ys + tid * P;
       const float* hr = Hs + tid * P;
       float* wr = Ws + tid * P;
-      if (U) {  // Y_r = U_r M  (LAI product fused into the update)
-        const float* ur = Us + tid * (l + 1);
-        for (int c = 0; c < RW; ++c) yr[c] = 0.f;
-        for (int p = 0; p < l; ++p) {
-          const float u = ur[p];
-          const float* mrow = Ms + p * RW;
-          for (int c = 0; c < RW; ++c) yr[c] = fmaf(u, mrow[c], yr[c]);
-        }
-      }
       for (int g = 0; g < ng; ++g) {
         const float* Gg = Gs + g * k * k;
         const int o = g * k;
+        float y[KMAX];
+        if (U) {  // Y_r = U_r M (LAI product fused into the update), in registers
+          const float* ur = Us + tid * (l + 1);
+#pragma unroll
+          for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
+          for (int p = 0; p < l; ++p) {
+            const float u = ur[p];
+            const float* mrow = Ms + p * RW + o;
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c)
+              if (c < k) y[c] = fmaf(u, mrow[c], y[c]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < KMAX; ++c) y[c] = c < k ? yr[o + c] : 0.f;
+        }
         float w[KMAX];
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) w[j] = j < k ? wr[o + j] : 0.f;
 #pragma unroll
         for (int i = 0; i < KMAX; ++i) {
           if (i < k) {
-            float acc = fmaf(alpha, hr[o + i], yr[o + i]);
+            // two independent chains halve the FMA latency of the column update
+            float a0 = fmaf(alpha, hr[o + i], y[i]), a1 = 0.f;
 #pragma unroll
             for (int j = 0; j < KMAX; ++j)
-              if (j != i && j < k) acc = fmaf(-w[j], Gg[j * k + i], acc);
-            w[i] = fmaxf(acc * inv[o + i], 0.f);
+              if (j != i && j < k) {
+                if (j & 1)
+                  a1 = fmaf(-w[j], Gg[j * k + i], a1);
+                else
+                  a0 = fmaf(-w[j], Gg[j * k + i], a0);
+              }
+            w[i] = fmaxf((a0 + a1) * inv[o + i], 0.f);
           }
         }
 #pragma unroll
@@ -405,17 +431,15 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
           if (j < k) {
             if (!isfinite(w[j])) bad = true;
             wr[o + j] = w[j];
-            tr += (double)w[j] * (double)yr[o + j];
+            tr += (double)w[j] * (double)y[j];
             const float d = w[j] - hr[o + j];
             dd += (double)d * (double)d;
           }
       }
     }
     __syncthreads();
-    for (int e = tid; e < rows * RW; e += HALS_ROWS) {
-      const int rr = e / RW, c = e - rr * RW;
-      Fu[(base + rr) * RW + c] = Ws[rr * P + c];
-    }
+    for (int rr = tid >> 5; rr < rows; rr += HALS_ROWS / 32)
+      for (int c = tid & 31; c < RW; c += 32) Fu[(base + rr) * RW + c] = Ws[rr * P + c];
     __syncthreads();
   }
   if (bad) set_error(err, ERR_NAN);
@@ -510,40 +534,56 @@ cudaError_t apply_small(const float* A, int lda, int la, const float* B, int lb,
 
 // ------------------------------------------------------------- leverage
 
+constexpr int LEV_ROWS = 128;
+
+// One thread per row; the block's rows are staged through shared memory with
+// coalesced loads (row pitch k + 1 avoids bank conflicts).
 template <int KMAX>
-__global__ void leverage_kernel(const float* __restrict__ F, int64_t n, int k,
-                                const float* __restrict__ Rinv, double* lev) {
+__global__ void __launch_bounds__(LEV_ROWS) leverage_kernel(const float* __restrict__ F, int64_t n, int k,
+                                                            const float* __restrict__ Rinv, double* lev) {
   __shared__ float Rs[KMAX * KMAX];
+  __shared__ float Fs[LEV_ROWS * (KMAX + 1)];
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rs[e] = Rinv[e];
+  const int64_t base = (int64_t)blockIdx.x * LEV_ROWS;
+  const int rows = (int)min((int64_t)LEV_ROWS, n - base);
+  for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
+    const int rr = e / k, c = e - rr * k;
+    Fs[rr * (k + 1) + c] = F[base * k + e];
+  }
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if ((int)threadIdx.x >= rows) return;
   float h[KMAX];
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j) h[j] = j < k ? F[i * k + j] : 0.f;
+  for (int j = 0; j < KMAX; ++j) h[j] = j < k ? Fs[threadIdx.x * (k + 1) + j] : 0.f;
   float s = 0.f;
   // z_j = sum_{p <= j} h_p Rinv[p][j]  (Rinv upper triangular)
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
-      float z = 0.f;
+      float z0 = 0.f, z1 = 0.f;
 #pragma unroll
-      for (int p = 0; p <= j; ++p) z = fmaf(h[p], Rs[p * k + j], z);
+      for (int p = 0; p <= j; ++p) {
+        if (p & 1)
+          z1 = fmaf(h[p], Rs[p * k + j], z1);
+        else
+          z0 = fmaf(h[p], Rs[p * k + j], z0);
+      }
+      const float z = z0 + z1;
       s = fmaf(z, z, s);
     }
   }
-  lev[i] = (double)s;
+  lev[base + threadIdx.x] = (double)s;
 }
 
 cudaError_t leverage_rows(const float* F, int64_t n, int k, const float* Rinv, double* lev,
                           cudaStream_t st) {
-  const int grid = (int)((n + 127) / 128);
+  const int grid = (int)((n + LEV_ROWS - 1) / LEV_ROWS);
   if (k <= 16)
-    leverage_kernel<16><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+    leverage_kernel<16><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
   else if (k <= 32)
-    leverage_kernel<32><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+    leverage_kernel<32><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
   else if (k <= 64)
-    leverage_kernel<64><<<grid, 128, 0, st>>>(F, n, k, Rinv, lev);
+    leverage_kernel<64><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
   else
     return cudaErrorInvalidValue;
   count_launches(1);

@@ -81,12 +81,13 @@ def test_batched_bf16_grouped_launch_reaches_oracle_residual(S):
 
 
 def test_batched_objectives_monotone_and_graph_replay(S):
-    Xs, Xn = _problems(torch.bfloat16)
+    # FP32 products: monotone up to FP32 rounding of the trace-trick terms
+    Xs, Xn = _problems(torch.float32)
     b = _batch(S, Xs, R=2)
     b.init_random(scaled=True)
     obj = b.sweep(30)
     nx = np.array([(X * X).sum() for X in Xn for _ in range(2)])
-    assert (np.diff(obj, axis=0) <= 1e-6 * nx).all()
+    assert (np.diff(obj, axis=0) <= 1e-7 * nx).all()
     n0 = S.launch_count()
     b.sweep(10, record=False)
     assert S.launch_count() > n0  # graph replays are counted per kernel node

@@ -45,19 +45,37 @@ def test_exact_range_capture_rank_deficient(S):
     assert np.linalg.norm(X - A) / np.linalg.norm(X) < 1e-5
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_lai_sweeps_match_oracle(S, use_graph):
+@pytest.mark.parametrize("mode", ["engine", "graph", "eager"])
+def test_lai_sweeps_match_oracle(S, mode):
+    # sweeps on the oracle's own U, Lambda (given through symnmf_set_lai): parity of the
+    # LAI-SymNMF loop itself, independent of the sketch's FP32 rounding
+    X, _ = _gmm_kernel(3000, 10, 6, seed=4)
+    k, l, q = 6, 22, 2
+    U, lam = O.apx_evd(X, gaussian_sketch(3000, l, seed=5), q)
+    Hi = uniform_factor(3000, k, seed=6) * O.init_scale(X, k)
+    s = S.Solver(t32(X), k, max_width=l, use_graph=(mode == "graph"), lai_mode=(0 if mode == "engine" else 1))
+    s.set_lai(t32(U), lam)
+    s.set_factors(t32(Hi))
+    got = s.sweep(100, source=S.SRC_LAI)
+    Uf = U.astype(np.float32).astype(np.float64)
+    _, _, ref = O.lai_symnmf(Uf, lam, Hi.astype(np.float32).astype(np.float64), O.default_alpha(X), 100)
+    assert rel_err(got, ref).max() < 1e-4
+
+
+def test_lai_sketch_then_sweeps_reach_oracle_residual(S):
+    # end to end: GPU sketch (same Omega) + 100 LAI sweeps; final true residual vs the oracle's
     X, _ = _gmm_kernel(3000, 10, 6, seed=4)
     k, l, q = 6, 22, 2
     Om = gaussian_sketch(3000, l, seed=5)
     Hi = uniform_factor(3000, k, seed=6) * O.init_scale(X, k)
-    s = S.Solver(t32(X), k, max_width=l, use_graph=use_graph)
+    s = S.Solver(t32(X), k, max_width=l)
     s.lai_sketch(l, q, t32(Om))
     s.set_factors(t32(Hi))
-    got = s.sweep(100, source=S.SRC_LAI)
+    s.sweep(100, source=S.SRC_LAI, record=False)
+    nr, _ = s.residual(S.SRC_X)
     U, lam = O.apx_evd(X, Om, q)
-    _, _, ref = O.lai_symnmf(U, lam, Hi.astype(np.float32).astype(np.float64), O.default_alpha(X), 100)
-    assert rel_err(got, ref).max() < 1e-4
+    W, H, _ = O.lai_symnmf(U, lam, Hi, O.default_alpha(X), 100, record=False)
+    assert abs(nr - O.normalized_residual(X, W, H)) <= 1e-4 * O.normalized_residual(X, W, H)
 
 
 def test_lai_bf16_then_fp32_refinement_reaches_oracle_residual(S):
@@ -93,3 +111,22 @@ def test_lai_fp8_sketch_is_close(S):
     nr, _ = s.residual(S.SRC_XHI)
     W, H, _ = O.hals_symnmf(X, Hi, O.default_alpha(X), 60, record=False)
     assert nr <= O.normalized_residual(X, W, H) + 1e-3
+
+
+@pytest.mark.parametrize("n,k,l", [(20000, 20, 50), (5003, 32, 74), (777, 64, 96), (50, 3, 8)])
+def test_lai_engine_and_per_kernel_path_match_oracle(S, n, k, l):
+    # both LAI sweep implementations on the oracle's U, Lambda of a rank-l operator
+    rng = np.random.default_rng(n)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, l)))
+    lam = np.sort(rng.uniform(0.1, 50.0, size=l))[::-1] * rng.choice([1, 1, 1, -1], size=l)
+    Hi = rng.random((n, k)) * 0.1
+    Uf = Q.astype(np.float32).astype(np.float64)
+    alpha = 1.0
+    _, Href, ref = O.lai_symnmf(Uf, lam, Hi.astype(np.float32).astype(np.float64), alpha, 30)
+    Xdummy = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    for mode in (0, 1):
+        s = S.Solver(Xdummy, k, max_width=l, lai_mode=mode, alpha=alpha)
+        s.set_lai(t32(Q), lam)
+        s.set_factors(t32(Hi))
+        got = s.sweep(30, source=S.SRC_LAI)
+        assert rel_err(got, ref).max() < 1e-4, (mode, rel_err(got, ref).max())

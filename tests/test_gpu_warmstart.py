@@ -1,0 +1,21 @@
+"""The learned warm start: trained on solver output, it must beat the random start it replaces."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_training_and_gain(S):
+    from paper_2402_08134_gb300 import warmstart as WS
+
+    out = WS.experiment(n=3000, d=16, c=8, k=8, l=26, q=2, sweeps=60, n_train=16, n_test=3, epochs=20,
+                        lr=2e-3, train_seeds=500, test_seeds=0)
+    losses = out["losses"]
+    assert losses[-1] < 0.8 * losses[0]
+    obj0_gain = [r["random"]["obj0"] / r["learned"]["obj0"] for r in out["rows"]]
+    # the learned start fits X better than the scaled random start at the first sweep
+    assert np.median(obj0_gain) > 1.0, out["rows"]
+    # and every held-out run reaches the random start's final objective
+    for r in out["rows"]:
+        assert r["learned"]["sweeps_to_target"] is not None or r["learned"]["nr"] <= r["random"]["nr"] + 1e-3
