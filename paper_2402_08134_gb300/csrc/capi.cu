@@ -410,7 +410,7 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
   TRY(dalloc(h, &h->eng_part, lai_engine_part_doubles(L, h->k)));
   TRY(dalloc(h, &h->eng_fin, lai_engine_fin_doubles(L, h->k)));
   TRY(dalloc(h, &h->eng_G, (size_t)2 * h->k * h->k));
-  TRY(dalloc(h, &h->eng_bar, 2));
+  TRY(dalloc(h, &h->eng_bar, 64));  // counter and generation in separate 128-byte lines
   h->lai_cap = L;
   TRYS(ensure_gemm_ws(h, L));
   return SYMNMF_OK;

@@ -9,8 +9,8 @@
 // engine runs every sweep in ONE cooperative launch (one CTA per SM):
 //
 //   per half sweep
-//     1. each CTA updates its rows (tiles of 128 rows staged in shared
-//        memory; Y_r = U_r M in registers; columns in order, each using the
+//     1. each CTA updates its rows (tiles of up to 256 rows staged once in
+//        shared memory; Y_r = U_r M in registers; columns in order, each using the
 //        ones already updated) and accumulates, over its rows, FP32 partials
 //        of U^T F_upd, F_upd^T F_upd, and FP64 sum F_upd .* Y, ||F_upd - F_fix||^2;
 //     2. grid barrier;
@@ -35,7 +35,6 @@
 namespace symnmf {
 
 constexpr int LE_THREADS = 256;
-constexpr int LE_ROWS = 128;  // rows per staged tile (one updating thread per row)
 
 __device__ __forceinline__ uint64_t le_timer() {
   uint64_t t;
@@ -43,12 +42,17 @@ __device__ __forceinline__ uint64_t le_timer() {
   return t;
 }
 
-// Returns false (on every thread of the block) when the barrier gave up.
+// The arrival counter (bar[0]) and the generation word (bar[LE_GEN]) sit in
+// different 128-byte lines, so that the spinning readers of the generation do
+// not contend with the arrivals.  Returns false (on every thread of the
+// block) when the barrier gave up.
+constexpr int LE_GEN = 32;
+
 __device__ bool le_grid_sync(unsigned* bar, unsigned* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
+    volatile unsigned* gen = bar + LE_GEN;
     const unsigned g = *gen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u) + 1u;
@@ -56,11 +60,12 @@ __device__ bool le_grid_sync(unsigned* bar, unsigned* err) {
     if (arrived == gridDim.x) {
       atomicExch(bar, 0u);
       __threadfence();
-      atomicAdd(bar + 1, 1u);
+      atomicAdd(bar + LE_GEN, 1u);
     } else {
       const uint64_t t0 = le_timer();
       unsigned spins = 0;
       while (*gen == g) {
+        __nanosleep(32);
         if ((++spins & 63u) == 0) {
           if (*(volatile unsigned*)err & ERR_TIMEOUT) {
             ok = 0;
@@ -97,6 +102,7 @@ struct LaiArgs {
   double* Gout;          // [2][k*k] FP64 Grams after the last sweep: [0] H^T H, [1] W^T W
   unsigned* bar;
   unsigned* err;
+  int tile_rows;
 };
 
 // Layout of one partial / final record: l*k entries of U^T F, k*k of F^T F, then tr, dd.
@@ -105,16 +111,17 @@ __host__ __device__ inline int le_entries(int l, int k) { return l * k + k * k +
 template <int KMAX>
 __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const int k = a.k, l = a.l;
+  const int k = a.k, l = a.l, TR = a.tile_rows;
   const int E = le_entries(l, k);
   const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3;
-  float* Ms = sm;                       // l x k  (lambda-scaled)
-  float* Gs = Ms + l * k;               // k x k
-  float* inv = Gs + k * k;              // k
-  float* Us = inv + k4;                 // LE_ROWS x (l4 + 1)
-  float* Fx = Us + LE_ROWS * (l4 + 1);  // LE_ROWS x (k4 + 1): fixed factor rows
-  float* Fu = Fx + LE_ROWS * (k4 + 1);  // LE_ROWS x (k4 + 1): updated factor rows
-  float* red = Fu + LE_ROWS * (k4 + 1); // 256 * 16 floats: row-group combine
+  const int us = l4 + 1, fs = k4 + 1;   // odd row pitches: conflict-free per-row reads
+  float* Ms = sm;                        // l x k4, lambda-scaled, zero padded (float4 rows)
+  float* Gs = Ms + l * k4;               // k x k4, zero padded (symmetric: row i = column i)
+  float* inv = Gs + k * k4;              // k4
+  float* Us = inv + k4;                  // TR x us: U rows of the tile
+  float* Fx = Us + TR * us;              // TR x fs: fixed factor rows
+  float* Fu = Fx + TR * fs;              // TR x fs: rows being updated
+  float* red = Fu + TR * fs;             // LE_THREADS x 16: row-group combine
   __shared__ double shd[32];
 
   const int tid = threadIdx.x;
@@ -123,71 +130,87 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
   const int64_t r1 = (a.n * (blockIdx.x + 1)) / gridDim.x;
 
   // 4x4 tiles over [U^T F (l4/4 x k4/4 tiles) | F^T F (k4/4 x k4/4 tiles)]
-  const int tm = (l4 / 4) * (k4 / 4), tg = (k4 / 4) * (k4 / 4), T = tm + tg;
+  const int kt = k4 / 4;
+  const int tm = (l4 / 4) * kt, tg = kt * kt, T = tm + tg;
   const int RG = T >= LE_THREADS ? 1 : LE_THREADS / T;  // row groups
-  const int my_rg = tid / T;
-  const int TPT = (T + LE_THREADS - 1) / LE_THREADS;  // tiles per thread when T > threads
+  const int my_rg = T >= LE_THREADS ? 0 : tid / T;
+  const int TPT = (T + LE_THREADS - 1) / LE_THREADS;     // tiles per thread (<= 4)
+  float acc[4][16];
 
-  // ---- partials of (U^T F, F^T F) over this CTA's rows of F (F in global) ----
-  // also used for the prologue; tr / dd are passed in.
-  auto partials = [&](const float* F, const float* Fsmem_unused, double tr, double dd, double* dst) {
-    (void)Fsmem_unused;
-    float acc[4][16];
+  auto clear_acc = [&]() {
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[t][e] = 0.f;
-    for (int64_t b = r0; b < r1; b += LE_ROWS) {
-      const int rows = (int)min((int64_t)LE_ROWS, r1 - b);
-      for (int rr = wid; rr < LE_ROWS; rr += LE_THREADS / 32) {
-        const bool live = rr < rows;
-        for (int c = lane; c < l4; c += 32) Us[rr * (l4 + 1) + c] = (live && c < l) ? a.U[(b + rr) * l + c] : 0.f;
-        for (int c = lane; c < k4; c += 32) Fu[rr * (k4 + 1) + c] = (live && c < k) ? F[(b + rr) * k + c] : 0.f;
+  };
+
+  // stage U rows (and optionally the fixed rows) of tile [b, b + rows); pads are zero
+  auto stage = [&](int64_t b, int rows, const float* Ffix, const float* Fupd) {
+    for (int rr = wid; rr < TR; rr += LE_THREADS / 32) {
+      const bool live = rr < rows;
+      const int64_t g = b + rr;
+      for (int c = lane; c < l4; c += 32) Us[rr * us + c] = (live && c < l) ? a.U[g * l + c] : 0.f;
+      for (int c = lane; c < k4; c += 32) {
+        if (Ffix) Fx[rr * fs + c] = (live && c < k) ? Ffix[g * k + c] : 0.f;
+        Fu[rr * fs + c] = (live && c < k) ? Fupd[g * k + c] : 0.f;
       }
-      __syncthreads();
+    }
+  };
+
+  // accumulate this tile's rows of U^T Fu and Fu^T Fu into acc (FP32)
+  auto accumulate = [&](int rows) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (t >= TPT) break;
-        const int tile = (T >= LE_THREADS) ? tid + t * LE_THREADS : tid % T;
-        if (tile < T && my_rg < RG) {
-          const float* A;
-          int ai, strideA, bj;
-          if (tile < tm) {
-            ai = (tile / (k4 / 4)) * 4;
-            bj = (tile % (k4 / 4)) * 4;
-            A = Us;
-            strideA = l4 + 1;
-          } else {
-            const int g = tile - tm;
-            ai = (g / (k4 / 4)) * 4;
-            bj = (g % (k4 / 4)) * 4;
-            A = Fu;
-            strideA = k4 + 1;
+    for (int t = 0; t < 4; ++t) {
+      if (t >= TPT) break;
+      const int tile = (T >= LE_THREADS) ? tid + t * LE_THREADS : tid % T;
+      if (tile < T && my_rg < RG) {
+        const float* A;
+        int ai, sa, bj;
+        if (tile < tm) {
+          ai = (tile / kt) * 4;
+          bj = (tile % kt) * 4;
+          A = Us;
+          sa = us;
+        } else {
+          const int g = tile - tm;
+          ai = (g / kt) * 4;
+          bj = (g % kt) * 4;
+          A = Fu;
+          sa = fs;
+        }
+        for (int rr = my_rg; rr < rows; rr += RG) {
+          float av[4], bv[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            av[p] = A[rr * sa + ai + p];
+            bv[p] = Fu[rr * fs + bj + p];
           }
-          for (int rr = my_rg; rr < rows; rr += RG) {
-            float av[4], bv[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              av[p] = A[rr * strideA + ai + p];
-              bv[p] = Fu[rr * (k4 + 1) + bj + p];
-            }
+          for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc[t][p * 4 + q] = fmaf(av[p], bv[q], acc[t][p * 4 + q]);
-          }
+            for (int q = 0; q < 4; ++q) acc[t][p * 4 + q] = fmaf(av[p], bv[q], acc[t][p * 4 + q]);
         }
       }
-      __syncthreads();
     }
-    // combine row groups in shared memory (fixed order), write FP64 record
-    double* rec = dst + (size_t)blockIdx.x * E;
-    for (int t = 0; t < TPT && t < 4; ++t) {
+  };
+
+  // combine row groups (fixed order) and write this CTA's FP64 record
+  auto finish = [&](double tr, double dd) {
+    double* rec = a.part + (size_t)blockIdx.x * E;
+    for (int t = 0; t < TPT; ++t) {
       const int tile = (T >= LE_THREADS) ? tid + t * LE_THREADS : tid % T;
+      const int slot = (tile % LE_THREADS) * 16;
       for (int g = 0; g < RG; ++g) {
-        if (tile < T && my_rg == g)
+        if (tile < T && my_rg == g) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) red[(tile % LE_THREADS) * 16 + e] = (g == 0 ? 0.f : red[(tile % LE_THREADS) * 16 + e]) + acc[t][e];
+          for (int e = 0; e < 16; ++e) {
+            float v = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (u == t) v = acc[u][e];
+            red[slot + e] = (g == 0 ? 0.f : red[slot + e]) + v;
+          }
+        }
         __syncthreads();
       }
       if (tile < T && my_rg == 0) {
@@ -195,26 +218,26 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
         for (int e = 0; e < 16; ++e) {
           const int p = e >> 2, q = e & 3;
           if (tile < tm) {
-            const int i = (tile / (k4 / 4)) * 4 + p, j = (tile % (k4 / 4)) * 4 + q;
-            if (i < l && j < k) rec[i * k + j] = (double)red[(tile % LE_THREADS) * 16 + e];
+            const int i = (tile / kt) * 4 + p, j = (tile % kt) * 4 + q;
+            if (i < l && j < k) rec[i * k + j] = (double)red[slot + e];
           } else {
             const int g2 = tile - tm;
-            const int i = (g2 / (k4 / 4)) * 4 + p, j = (g2 % (k4 / 4)) * 4 + q;
-            if (i < k && j < k) rec[l * k + i * k + j] = (double)red[(tile % LE_THREADS) * 16 + e];
+            const int i = (g2 / kt) * 4 + p, j = (g2 % kt) * 4 + q;
+            if (i < k && j < k) rec[l * k + i * k + j] = (double)red[slot + e];
           }
         }
       }
       __syncthreads();
     }
-    double t2 = block_sum(tr, shd);
-    double d2 = block_sum(dd, shd);
+    const double t2 = block_sum(tr, shd);
+    const double d2 = block_sum(dd, shd);
     if (tid == 0) {
       rec[l * k + k * k] = t2;
       rec[l * k + k * k + 1] = d2;
     }
   };
 
-  // ---- sliced reduction of all CTA records into fin[slot] ----
+  // sliced reduction of all CTA records into fin (one warp per entry)
   auto reduce_slice = [&](double* fin) {
     const int per = (E + gridDim.x - 1) / gridDim.x;
     const int e0 = blockIdx.x * per, e1 = min(E, e0 + per);
@@ -226,66 +249,95 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
     }
   };
 
-  // ---- load M (lambda-scaled), G, inv from fin ----
+  // M (lambda-scaled), G, 1 / (G_ii + alpha) from fin
   auto load_state = [&](const double* fin) {
-    for (int e = tid; e < l * k; e += LE_THREADS) Ms[e] = (float)(a.lam[e / k] * __ldcg(fin + e));
-    for (int e = tid; e < k * k; e += LE_THREADS) Gs[e] = (float)__ldcg(fin + l * k + e);
+    for (int e = tid; e < l * k4; e += LE_THREADS) {
+      const int i = e / k4, j = e - i * k4;
+      Ms[e] = j < k ? (float)(a.lam[i] * __ldcg(fin + i * k + j)) : 0.f;
+    }
+    for (int e = tid; e < k * k4; e += LE_THREADS) {
+      const int i = e / k4, j = e - i * k4;
+      Gs[e] = j < k ? (float)__ldcg(fin + l * k + i * k + j) : 0.f;
+    }
     __syncthreads();
-    for (int i = tid; i < k; i += LE_THREADS) inv[i] = 1.0f / (Gs[i * k + i] + a.alpha);
+    for (int i = tid; i < k4; i += LE_THREADS) inv[i] = i < k ? 1.0f / (Gs[i * k4 + i] + a.alpha) : 0.f;
     __syncthreads();
   };
 
-  // prologue: state of the H side (W-update uses M = Lambda U^T H, G = H^T H)
-  partials(a.H, nullptr, 0.0, 0.0, a.part);
+  // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
+  clear_acc();
+  for (int64_t b = r0; b < r1; b += TR) {
+    const int rows = (int)min((int64_t)TR, r1 - b);
+    stage(b, rows, nullptr, a.H);
+    __syncthreads();
+    accumulate(rows);
+    __syncthreads();
+  }
+  finish(0.0, 0.0);
   if (!le_grid_sync(a.bar, a.err)) return;
   reduce_slice(a.fin + E);
   if (!le_grid_sync(a.bar, a.err)) return;
   load_state(a.fin + E);
 
+  const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
+  const float4* Gs4 = reinterpret_cast<const float4*>(Gs);
+  const int k4q = k4 / 4;
   for (int t = 0; t < a.nsweeps; ++t) {
     for (int side = 0; side < 2; ++side) {
       float* Fupd = side ? a.H : a.W;
       const float* Ffix = side ? a.W : a.H;
       double tr = 0.0, dd = 0.0;
       bool bad = false;
-      // 1. row updates (threads 0..LE_ROWS-1 own one row of each tile)
-      for (int64_t b = r0; b < r1; b += LE_ROWS) {
-        const int rows = (int)min((int64_t)LE_ROWS, r1 - b);
-        for (int rr = wid; rr < rows; rr += LE_THREADS / 32) {
-          for (int c = lane; c < l; c += 32) Us[rr * (l4 + 1) + c] = a.U[(b + rr) * l + c];
-          for (int c = lane; c < k; c += 32) {
-            Fx[rr * (k4 + 1) + c] = Ffix[(b + rr) * k + c];
-            Fu[rr * (k4 + 1) + c] = Fupd[(b + rr) * k + c];
-          }
-        }
+      clear_acc();
+      for (int64_t b = r0; b < r1; b += TR) {
+        const int rows = (int)min((int64_t)TR, r1 - b);
+        stage(b, rows, Ffix, Fupd);
         __syncthreads();
         if (tid < rows) {
-          const float* ur = Us + tid * (l4 + 1);
-          const float* hr = Fx + tid * (k4 + 1);
-          float* wr = Fu + tid * (k4 + 1);
+          const float* ur = Us + tid * us;
+          const float* hr = Fx + tid * fs;
+          float* wr = Fu + tid * fs;
           float y[KMAX], w[KMAX];
 #pragma unroll
           for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
+          // Y_r = U_r M  (LAI product), float4 broadcast reads of M's rows
           for (int p = 0; p < l; ++p) {
             const float u = ur[p];
 #pragma unroll
-            for (int c = 0; c < KMAX; ++c)
-              if (c < k) y[c] = fmaf(u, Ms[p * k + c], y[c]);
+            for (int c4 = 0; c4 < KMAX / 4; ++c4) {
+              if (c4 < k4q) {
+                const float4 m = Ms4[p * k4q + c4];
+                y[4 * c4 + 0] = fmaf(u, m.x, y[4 * c4 + 0]);
+                y[4 * c4 + 1] = fmaf(u, m.y, y[4 * c4 + 1]);
+                y[4 * c4 + 2] = fmaf(u, m.z, y[4 * c4 + 2]);
+                y[4 * c4 + 3] = fmaf(u, m.w, y[4 * c4 + 3]);
+              }
+            }
           }
 #pragma unroll
           for (int j = 0; j < KMAX; ++j) w[j] = j < k ? wr[j] : 0.f;
+          // columns in order, each using the columns already updated (G symmetric: row i)
 #pragma unroll
           for (int i = 0; i < KMAX; ++i) {
             if (i < k) {
               float a0 = fmaf(a.alpha, hr[i], y[i]), a1 = 0.f;
 #pragma unroll
-              for (int j = 0; j < KMAX; ++j)
-                if (j != i && j < k) {
-                  if (j & 1)
-                    a1 = fmaf(-w[j], Gs[j * k + i], a1);
-                  else
-                    a0 = fmaf(-w[j], Gs[j * k + i], a0);
+              for (int j4 = 0; j4 < KMAX / 4; ++j4) {
+                if (j4 < k4q) {
+                  const float4 g = Gs4[i * k4q + j4];
+                  const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const int j = 4 * j4 + u;
+                    if (j != i) {  // pads of G are zero, so j >= k adds nothing
+                      if (u & 1)
+                        a1 = fmaf(-w[j], gv[u], a1);
+                      else
+                        a0 = fmaf(-w[j], gv[u], a0);
+                    }
+                  }
                 }
+              }
               w[i] = fmaxf((a0 + a1) * inv[i], 0.f);
             }
           }
@@ -301,12 +353,12 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
         }
         __syncthreads();
         for (int rr = wid; rr < rows; rr += LE_THREADS / 32)
-          for (int c = lane; c < k; c += 32) Fupd[(b + rr) * k + c] = Fu[rr * (k4 + 1) + c];
+          for (int c = lane; c < k; c += 32) Fupd[(b + rr) * k + c] = Fu[rr * fs + c];
+        accumulate(rows);  // partials of the next half straight from shared memory
         __syncthreads();
       }
       if (bad) set_error(a.err, ERR_NAN);
-      // 1b. partials over the updated rows (re-read: the tiles above are overwritten)
-      partials(Fupd, nullptr, tr, dd, a.part);
+      finish(tr, dd);
       if (!le_grid_sync(a.bar, a.err)) return;
       double* fin = a.fin + (side == 0 ? 0 : E);
       reduce_slice(fin);
@@ -316,11 +368,11 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
         // objective after the sweep: sum lambda^2 + sum GW .* GH - 2 tr + alpha dd
         const double* fw = a.fin;
         const double* fh = a.fin + E;
-        double s = 0.0;
-        for (int e = tid; e < k * k; e += LE_THREADS) s += __ldcg(fw + l * k + e) * __ldcg(fh + l * k + e);
-        s = block_sum(s, shd);
+        double s2 = 0.0;
+        for (int e = tid; e < k * k; e += LE_THREADS) s2 += __ldcg(fw + l * k + e) * __ldcg(fh + l * k + e);
+        s2 = block_sum(s2, shd);
         if (tid == 0 && t < a.obj_cap)
-          a.obj[t] = a.normX2[0] + s - 2.0 * __ldcg(fh + l * k + k * k) + a.alpha_d * __ldcg(fh + l * k + k * k + 1);
+          a.obj[t] = a.normX2[0] + s2 - 2.0 * __ldcg(fh + l * k + k * k) + a.alpha_d * __ldcg(fh + l * k + k * k + 1);
       }
     }
   }
@@ -335,11 +387,16 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_engine_kernel(LaiArgs a) {
 size_t lai_engine_part_doubles(int l, int k) { return (size_t)num_sms() * le_entries(l, k); }
 size_t lai_engine_fin_doubles(int l, int k) { return (size_t)2 * le_entries(l, k); }
 
+static size_t engine_smem(int l, int k, int tr) {
+  const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3;
+  return (size_t)(l * k4 + k * k4 + k4 + tr * (l4 + 1) + 2 * tr * (k4 + 1) + LE_THREADS * 16) * sizeof(float);
+}
+
 template <int KMAX>
-static cudaError_t launch_engine(const LaiArgs& a, cudaStream_t st) {
-  const int l4 = (a.l + 3) & ~3, k4 = (a.k + 3) & ~3;
-  const size_t smem = (size_t)(a.l * a.k + a.k * a.k + k4 + LE_ROWS * (l4 + 1) + 2 * LE_ROWS * (k4 + 1) +
-                               LE_THREADS * 16) * sizeof(float);
+static cudaError_t launch_engine(LaiArgs a, cudaStream_t st) {
+  // one tile per CTA when it fits (n = 2e4 gives ~132 rows per CTA)
+  a.tile_rows = engine_smem(a.l, a.k, 256) <= 200 * 1024 ? 256 : 128;
+  const size_t smem = engine_smem(a.l, a.k, a.tile_rows);
   cudaError_t e = cudaFuncSetAttribute(lai_engine_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -349,8 +406,7 @@ static cudaError_t launch_engine(const LaiArgs& a, cudaStream_t st) {
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = num_sms();
   if ((int64_t)grid > a.n) grid = (int)std::max<int64_t>(1, a.n);
-  LaiArgs args = a;
-  void* params[] = {&args};
+  void* params[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)lai_engine_kernel<KMAX>, dim3(grid), dim3(LE_THREADS), params,
                                   smem, st);
   count_launches(1);
@@ -361,11 +417,14 @@ cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, in
                        int nsweeps, double alpha, const double* normX2, double* part, double* fin, double* obj,
                        int obj_cap, double* Gout, unsigned* bar, unsigned* err, cudaStream_t st) {
   if (k < 1 || k > 64 || l < 1 || l > 96 || n < 1) return cudaErrorInvalidValue;
-  LaiArgs a{U, lam, W, H, n, k, l, nsweeps, (float)alpha, alpha, normX2, part, fin, obj, obj_cap, Gout, bar, err};
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  LaiArgs a{U, lam, W, H, n, k, l, nsweeps, (float)alpha, alpha, normX2, part, fin, obj, obj_cap, Gout, bar, err, 256};
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * LE_GEN * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
+  if (k <= 8) return launch_engine<8>(a, st);
   if (k <= 16) return launch_engine<16>(a, st);
+  if (k <= 24) return launch_engine<24>(a, st);
   if (k <= 32) return launch_engine<32>(a, st);
+  if (k <= 48) return launch_engine<48>(a, st);
   return launch_engine<64>(a, st);
 }
 

@@ -45,14 +45,15 @@ __global__ void xstats_dense_kernel(int fmt, const void* x, int64_t ldx, const f
                                     double* out, double* ws, unsigned* counter) {
   __shared__ double sh[32];
   double mx = -INFINITY, sm = 0.0, sq = 0.0;
-  const int64_t total = n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e - i * n;
-    const double v = load_x(fmt, x, ldx, rs, i, j);
-    mx = fmax(mx, v);
-    sm += v;
-    sq += v * v;
+  // a block per row (strided), threads along the row: no index division; FP64 sums
+  // (||X||^2 enters the trace-trick objective, which cancels terms of its size)
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = load_x(fmt, x, ldx, rs, i, j);
+      mx = fmax(mx, v);
+      sm += v;
+      sq += v * v;
+    }
   }
   // block reductions (max via negation trick is not needed: use warp_max)
   mx = warp_max(mx);
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
       }
     }
   }
-  if (last_block<1>(counter)) {
+  if (counter && last_block<1>(counter)) {
     const unsigned G = gridDim.x;
     for (int e = tid; e < LL; e += XC_THREADS) {
       // four independent chains keep several L2 loads in flight (fixed order)
@@ -297,6 +298,25 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   }
 }
 
+// Second stage for large reductions: one warp per entry sums the block
+// partials (lanes strided over blocks, then a fixed shuffle tree).
+__global__ void xcross_reduce_kernel(const double* __restrict__ ws, int G, int LL, int lb,
+                                     const double* __restrict__ lam, double shift, double* C, float* Cf) {
+  const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= LL) return;
+  double s = 0.0;
+  for (int b = lane; b < G; b += 32) s += __ldcg(ws + (size_t)b * LL + e);
+  s = warp_sum(s);
+  if (lane == 0) {
+    const int i = e / lb, j = e - i * lb;
+    if (lam) s *= lam[i];
+    if (i == j) s += shift;
+    if (C) C[e] = s;
+    if (Cf) Cf[e] = (float)s;
+  }
+}
+
 cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int lb, int64_t n,
                    const int32_t* idx, const float* wt, const int* cnt, const double* lam,
                    double shift, double* C, float* Cf, double* ws, unsigned* counter,
@@ -309,24 +329,34 @@ cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int
   const int cap = num_sms() * ((size_t)la * lb <= 4096 ? 2 : 1);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
+  // many partials of many entries: reduce them with the whole GPU instead of one block
+  const int LL = la * lb;
+  const bool two_stage = grid >= 16 && (int64_t)grid * LL > 16384;
+  unsigned* ctr = two_stage ? nullptr : counter;
   cudaError_t e;
   if (T <= XC_THREADS) {
     e = cudaFuncSetAttribute(xcross_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     xcross_kernel<1><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, counter);
+                                                     shift, C, Cf, ws, ctr);
   } else if (T <= 2 * XC_THREADS) {
     e = cudaFuncSetAttribute(xcross_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     xcross_kernel<2><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, counter);
+                                                     shift, C, Cf, ws, ctr);
   } else {
     e = cudaFuncSetAttribute(xcross_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     xcross_kernel<4><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, counter);
+                                                     shift, C, Cf, ws, ctr);
   }
   count_launches(1);
+  if (two_stage) {
+    const int warps_per_block = 8;
+    xcross_reduce_kernel<<<(LL + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        ws, grid, LL, lb, lam, shift, C, Cf);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -345,24 +375,34 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
     unsigned* counter, unsigned* err) {
   extern __shared__ __align__(16) float sm[];
   const int RW = ng * k;         // row width
-  const int P = RW + 1;          // padded smem row stride
-  float* Gs = sm;                // ng*k*k
-  float* inv = Gs + ng * k * k;  // ng*k
-  float* Ys = inv + ng * k;      // HALS_ROWS * P
+  const int P = RW + 1;          // odd smem row pitch: conflict-free per-row reads
+  const int k4 = (k + 3) & ~3, k4q = k4 / 4;
+  float* Gs = sm;                  // ng x k x k4, zero padded (G symmetric: row i = column i)
+  float* inv = Gs + ng * k * k4;   // ng x k4
+  float* Ms = inv + ng * k4;       // l x k4 (LAI only, ng == 1), zero padded
+  float* Ys = Ms + (U ? l * k4 : 0);  // HALS_ROWS x P
   float* Hs = Ys + HALS_ROWS * P;
   float* Ws = Hs + HALS_ROWS * P;
-  float* Us = Ws + HALS_ROWS * P;  // HALS_ROWS * (l+1)   (LAI only)
-  float* Ms = Us + (U ? HALS_ROWS * (l + 1) : 0);  // l * RW (LAI only)
+  float* Us = Ws + HALS_ROWS * P;  // HALS_ROWS x (l + 1) (LAI only)
   const int tid = threadIdx.x;
-  for (int e = tid; e < ng * k * k; e += HALS_ROWS) Gs[e] = G[e];
-  __syncthreads();
-  for (int e = tid; e < ng * k; e += HALS_ROWS) {
-    const int g = e / k, i = e - g * k;
-    inv[e] = 1.0f / (Gs[g * k * k + i * k + i] + alpha);
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < ng * k * k4; e += HALS_ROWS) {
+    const int gi = e / k4, j = e - gi * k4;  // gi = g * k + i
+    Gs[e] = j < k ? G[gi * k + j] : 0.f;
   }
   if (U)
-    for (int e = tid; e < l * RW; e += HALS_ROWS) Ms[e] = M[e];
+    for (int e = tid; e < l * k4; e += HALS_ROWS) {
+      const int i = e / k4, j = e - i * k4;
+      Ms[e] = j < k ? M[i * k + j] : 0.f;
+    }
   __syncthreads();
+  for (int e = tid; e < ng * k4; e += HALS_ROWS) {
+    const int g = e / k4, i = e - g * k4;
+    inv[e] = i < k ? 1.0f / (Gs[(g * k + i) * k4 + i] + alpha) : 0.f;
+  }
+  __syncthreads();
+  const float4* Gs4 = reinterpret_cast<const float4*>(Gs);
+  const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
 
   double tr = 0.0, dd = 0.0;
   bool bad = false;
@@ -370,9 +410,7 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t base = tile * HALS_ROWS;
     const int rows = (int)min((int64_t)HALS_ROWS, n - base);
-    // coalesced staging of the tile's rows
     // coalesced staging, one warp per row (no index division)
-    const int lane = tid & 31, wid = tid >> 5;
     for (int rr = wid; rr < rows; rr += HALS_ROWS / 32) {
       const int64_t g = (base + rr);
       for (int c = lane; c < RW; c += 32) {
@@ -389,8 +427,8 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
       const float* hr = Hs + tid * P;
       float* wr = Ws + tid * P;
       for (int g = 0; g < ng; ++g) {
-        const float* Gg = Gs + g * k * k;
         const int o = g * k;
+        const float4* Gg4 = Gs4 + (size_t)g * k * k4q;
         float y[KMAX];
         if (U) {  // Y_r = U_r M (LAI product fused into the update), in registers
           const float* ur = Us + tid * (l + 1);
@@ -398,10 +436,15 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
           for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
           for (int p = 0; p < l; ++p) {
             const float u = ur[p];
-            const float* mrow = Ms + p * RW + o;
 #pragma unroll
-            for (int c = 0; c < KMAX; ++c)
-              if (c < k) y[c] = fmaf(u, mrow[c], y[c]);
+            for (int c4 = 0; c4 < KMAX / 4; ++c4)
+              if (c4 < k4q) {
+                const float4 m = Ms4[p * k4q + c4];
+                y[4 * c4 + 0] = fmaf(u, m.x, y[4 * c4 + 0]);
+                y[4 * c4 + 1] = fmaf(u, m.y, y[4 * c4 + 1]);
+                y[4 * c4 + 2] = fmaf(u, m.z, y[4 * c4 + 2]);
+                y[4 * c4 + 3] = fmaf(u, m.w, y[4 * c4 + 3]);
+              }
           }
         } else {
 #pragma unroll
@@ -416,14 +459,22 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
             // two independent chains halve the FMA latency of the column update
             float a0 = fmaf(alpha, hr[o + i], y[i]), a1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < KMAX; ++j)
-              if (j != i && j < k) {
-                if (j & 1)
-                  a1 = fmaf(-w[j], Gg[j * k + i], a1);
-                else
-                  a0 = fmaf(-w[j], Gg[j * k + i], a0);
+            for (int j4 = 0; j4 < KMAX / 4; ++j4)
+              if (j4 < k4q) {
+                const float4 gq = Gg4[i * k4q + j4];
+                const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int j = 4 * j4 + u;
+                  if (j != i) {  // zero pads: j >= k adds nothing
+                    if (u & 1)
+                      a1 = fmaf(-w[j], gv[u], a1);
+                    else
+                      a0 = fmaf(-w[j], gv[u], a0);
+                  }
+                }
               }
-            w[i] = fmaxf((a0 + a1) * inv[o + i], 0.f);
+            w[i] = fmaxf((a0 + a1) * inv[g * k4 + i], 0.f);
           }
         }
 #pragma unroll
@@ -461,14 +512,15 @@ static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, int
                                double alpha, const float* Y, int ldy, const float* U, int l,
                                const float* M, double* part, double* ws, unsigned* counter,
                                unsigned* err, cudaStream_t st) {
-  const int RW = ng * k, P = RW + 1;
-  size_t smem = (size_t)(ng * k * k + ng * k + 3 * HALS_ROWS * P) * 4;
-  if (U) smem += (size_t)(HALS_ROWS * (l + 1) + l * RW) * 4;
+  if (U && ng != 1) return cudaErrorInvalidValue;
+  const int RW = ng * k, P = RW + 1, k4 = (k + 3) & ~3;
+  size_t smem = (size_t)(ng * k * k4 + ng * k4 + 3 * HALS_ROWS * P) * 4;
+  if (U) smem += (size_t)(HALS_ROWS * (l + 1) + l * k4) * 4;
   cudaError_t e = cudaFuncSetAttribute(hals_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (n + HALS_ROWS - 1) / HALS_ROWS;
-  int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 8);
+  int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 4);
   if (grid < 1) grid = 1;
   hals_kernel<KMAX><<<grid, HALS_ROWS, smem, st>>>(Fu, Ff, n, k, ng, G, (float)alpha, Y, ldy, U, l, M,
                                                    part, ws, counter, err);

@@ -99,41 +99,42 @@ cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, 
 
 // Cyclic two-sided Jacobi with the round-robin (circle) ordering: each round
 // rotates l/2 disjoint pairs at once (Golub & Van Loan, symmetric Schur 2x2).
+// Rotations run in FP32 (GB300's FP64 rate is ~1/64 of FP32 and T is only
+// l x l); the convergence sums are FP64.  Eigenvectors come out orthonormal
+// to ~1e-7, far below the precision of the products that formed T.
 __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* lam) {
-  extern __shared__ double sm[];
+  extern __shared__ float smf[];
   const int L = (l + 1) & ~1;  // padded to even; index l is a dummy when l is odd
-  double* A = sm;              // l*l
-  double* V = A + l * l;       // l*l
-  double* cs = V + l * l;      // 2 * (L/2)
+  float* A = smf;              // l*l
+  float* V = A + l * l;        // l*l
+  float* cs = V + l * l;       // 2 * (L/2)
   int* pp = (int*)(cs + L);    // L/2
   int* qq = pp + L / 2;
   __shared__ double off, tot;
+  __shared__ double shr[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < l * l; e += nt) {
     const int i = e / l, j = e - i * l;
-    A[e] = 0.5 * (Ain[i * l + j] + Ain[j * l + i]);
-    V[e] = (i == j) ? 1.0 : 0.0;
+    A[e] = (float)(0.5 * (Ain[i * l + j] + Ain[j * l + i]));
+    V[e] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
   const int m = L / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    {
-      __shared__ double shr[32];
-      double o = 0.0, t = 0.0;
-      for (int e = tid; e < l * l; e += nt) {
-        const double v = A[e] * A[e];
-        t += v;
-        if (e / l != e % l) o += v;
-      }
-      o = block_sum(o, shr);
-      t = block_sum(t, shr);
-      if (tid == 0) {
-        off = o;
-        tot = t;
-      }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double o = 0.0, t = 0.0;
+    for (int e = tid; e < l * l; e += nt) {
+      const double v = (double)A[e] * (double)A[e];
+      t += v;
+      if (e / l != e % l) o += v;
+    }
+    o = block_sum(o, shr);
+    t = block_sum(t, shr);
+    if (tid == 0) {
+      off = o;
+      tot = t;
     }
     __syncthreads();
-    if (off <= 1e-28 * tot || off == 0.0) break;
+    if (off <= 1e-13 * tot || off == 0.0) break;
     for (int round = 0; round < L - 1; ++round) {
       // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate
       for (int i = tid; i < m; i += nt) {
@@ -141,14 +142,14 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
         const int bslot = L - 1 - i;
         const int b = ((bslot - 1 + round) % (L - 1)) + 1;
         int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
+        float c = 1.f, s = 0.f;
         if (q < l) {
-          const double apq = A[p * l + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * l + q] - A[p * l + p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
+          const float apq = A[p * l + q];
+          if (apq != 0.f) {
+            const float tau = (A[q * l + q] - A[p * l + p]) / (2.f * apq);
+            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = 1.f / sqrtf(1.f + tt * tt);
+            s = tt * c;
           }
         } else {
           p = -1;
@@ -164,8 +165,8 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
         const int i = e / l, col = e - i * l;
         const int p = pp[i], q = qq[i];
         if (p < 0) continue;
-        const double c = cs[2 * i], s = cs[2 * i + 1];
-        const double ap = A[p * l + col], aq = A[q * l + col];
+        const float c = cs[2 * i], s = cs[2 * i + 1];
+        const float ap = A[p * l + col], aq = A[q * l + col];
         A[p * l + col] = c * ap - s * aq;
         A[q * l + col] = s * ap + c * aq;
       }
@@ -175,25 +176,25 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
         const int i = e / l, row = e - i * l;
         const int p = pp[i], q = qq[i];
         if (p < 0) continue;
-        const double c = cs[2 * i], s = cs[2 * i + 1];
-        const double ap = A[row * l + p], aq = A[row * l + q];
+        const float c = cs[2 * i], s = cs[2 * i + 1];
+        const float ap = A[row * l + p], aq = A[row * l + q];
         A[row * l + p] = c * ap - s * aq;
         A[row * l + q] = s * ap + c * aq;
-        const double vp = V[row * l + p], vq = V[row * l + q];
+        const float vp = V[row * l + p], vq = V[row * l + q];
         V[row * l + p] = c * vp - s * vq;
         V[row * l + q] = s * vp + c * vq;
       }
       __syncthreads();
     }
   }
-  for (int e = tid; e < l * l; e += nt) Vout[e] = V[e];
-  for (int i = tid; i < l; i += nt) lam[i] = A[i * l + i];
+  for (int e = tid; e < l * l; e += nt) Vout[e] = (double)V[e];
+  for (int i = tid; i < l; i += nt) lam[i] = (double)A[i * l + i];
 }
 
 cudaError_t jacobi_evd(const double* A, int l, double* V, double* lam, cudaStream_t st) {
   if (l < 1 || l > 96) return cudaErrorInvalidValue;
   const int L = (l + 1) & ~1;
-  const size_t smem = (size_t)2 * l * l * 8 + (size_t)L * 8 + (size_t)L * 4 + 16;
+  const size_t smem = (size_t)2 * l * l * 4 + (size_t)L * 4 + (size_t)L * 4 + 16;
   cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -122,7 +122,9 @@ def experiment(n=50000, d=64, c=32, k=32, l=74, q=2, sweeps=200, n_train=200, n_
         row = {}
         for name in ("random", "learned"):
             sw = sweeps_to_target(res[name]["objs"], target * (1 + 1e-6))
-            row[name] = dict(sweeps_to_target=sw, obj0=float(res[name]["objs"][0]), nr=res[name]["nr"],
+            o = res[name]["objs"]
+            row[name] = dict(sweeps_to_target=sw, obj0=float(o[0]), obj5=float(o[min(4, len(o) - 1)]),
+                             obj10=float(o[min(9, len(o) - 1)]), obj_final=float(o[-1]), nr=res[name]["nr"],
                              seconds=res[name]["seconds"])
         rows.append(row)
         del Xf, Xb
