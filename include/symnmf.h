@@ -212,6 +212,19 @@ symnmf_status symnmf_csr_xf(const int64_t* row_ptr, const int32_t* col, const fl
                             const float* F, int N, float* Y, void* stream);
 /* G = F^T F in FP64 (device double[N x N]); F device float [n x N]. */
 symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G, void* stream);
+/* The same Gram matrix as symnmf_gram, computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not call cudaMalloc or an allocating library, e.g. code that runs where the
+ * device memory is owned by someone else (a host application's fixed pool or
+ * a real-time loop that forbids allocation).  The kernel's scratch for block
+ * partials lives in a static device array of 16 MiB (plus one counter) that
+ * every GPU that loads this library holds until the process exits.  Limits:
+ * N <= 64 (SYMNMF_EINVAL beyond) and at most 256 SMs (SYMNMF_EUNSUPPORTED).
+ * The first call on a device looks up the array's device address for that
+ * device.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Stream-ordered, no synchronisation. */
+symnmf_status symnmf_gram_noalloc(const float* F, int64_t n, int N, double* G, void* stream);
 /* Philox Gaussian Omega (device float [n x l]) as in symnmf_lai_sketch. */
 symnmf_status symnmf_gaussian(float* out, int64_t n, int l, uint64_t seed, void* stream);
 /* FP8 copy of a dense float X: row_scale_i = max_j |X_ij| / 448, x8 = e4m3(X / row_scale). */

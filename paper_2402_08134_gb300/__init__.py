@@ -87,6 +87,7 @@ _SIGS = {
     "symnmf_dense_xf": (_I, [_I, _P, _I64, _P, _I64, _P, _I, _I, _P, _I, _I, _P]),
     "symnmf_csr_xf": (_I, [_P, _P, _P, _I64, _P, _I, _P, _P]),
     "symnmf_gram": (_I, [_P, _I64, _I, _P, _P]),
+    "symnmf_gram_noalloc": (_I, [_P, _I64, _I, _P, _P]),
     "symnmf_gaussian": (_I, [_P, _I64, _I, C.c_uint64, _P]),
     "symnmf_quantize_fp8": (_I, [_P, _I64, _I64, _P, _I64, _P, _P]),
     "symnmf_convert_bf16": (_I, [_P, _I64, _I64, _P, _I64, _P]),
