@@ -104,8 +104,12 @@ typedef struct {
   int32_t use_graph;  /* 1: record sweep bodies as CUDA graphs once and replay them */
   int32_t max_width;  /* largest sketch width l to be requested (0: 2k + 10); <= 128 */
   int32_t max_samples;/* largest sample count s for LvS calls (0: n) */
-  int32_t lai_mode;   /* LAI-HALS sweeps: 0 = one persistent cooperative launch for
-                         all sweeps (default), 1 = separate kernels per step */
+  int32_t lai_mode;   /* LAI steps: 0 = persistent cooperative launches (all
+                         LAI-HALS sweeps in one, each CholeskyQR3 of the range
+                         finder in one), rows kept in shared memory when they
+                         fit (default); 1 = separate kernels per step; 2 = as
+                         0 but the sweep launch streams its rows from global
+                         memory every half sweep */
   int32_t reserved[3];
 } symnmf_options;
 

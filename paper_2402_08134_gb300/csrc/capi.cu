@@ -411,34 +411,21 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
   TRY(dalloc(h, &h->eng_fin, lai_engine_fin_doubles(L, h->k)));
   TRY(dalloc(h, &h->eng_G, (size_t)2 * h->k * h->k));
   TRY(dalloc(h, &h->eng_bar, 64));  // counter and generation in separate 128-byte lines
+  TRY(dalloc(h, &h->cq_part, cholqr_part_doubles(L)));
+  TRY(dalloc(h, &h->cq_fin, (size_t)L * L));
+  TRY(dalloc(h, &h->cq_Rf, (size_t)L * (L + 3)));
+  TRY(dalloc(h, &h->cq_rinv, (size_t)L + 3));
   h->lai_cap = L;
   TRYS(ensure_gemm_ws(h, L));
   return SYMNMF_OK;
 }
 
 // Rank-safe orthonormalisation of S (n x l) in place, T scratch (n x l):
-// shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
-// SIAM J. Sci. Comput. 2020).  Pass 1 factors S^T S + 1e-6 max_i (S^T S)_ii I,
-// which is positive definite whatever the rank of S; passes 2 and 3 are
-// plain CholeskyQR.  Gram matrices are accumulated in FP64 and factored in
-// FP64; pivots below 1e-10 of the largest diagonal entry are dropped (a zero
-// column of Q), so a rank-deficient sketch keeps exactly its numerical range.
+// shifted CholeskyQR3 (cholqr.cu), one cooperative launch unless the handle
+// asks for separate kernels per step.
 static symnmf_status orth(symnmf_t h, float* S, float* T, int l) {
-  const int64_t n = h->n;
-  float* src = S;
-  float* dst = T;
-  for (int pass = 0; pass < 3; ++pass) {
-    TRY(xcross(src, l, l, src, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
-               h->counters + 0, h->st));
-    TRY(chol_inverse(h->Sm_d, l, pass == 0 ? -1e-6 : 0.0, pass == 0 ? 1e-12 : 1e-10, nullptr, h->Rl_f, h->err,
-                     h->st));
-    TRY(apply_small(src, l, l, h->Rl_f, l, n, dst, l, h->st));
-    float* t = src;
-    src = dst;
-    dst = t;
-  }
-  // three passes: the result is in T; copy back into S
-  TRY(cudaMemcpyAsync(S, src, (size_t)n * l * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  TRY(cholqr3(S, T, h->n, l, h->cq_part, h->cq_fin, h->Sm_d, h->cq_Rf, h->cq_rinv, h->ws, h->counters + 0,
+              h->eng_bar, h->err, h->o.lai_mode != 1, h->st));
   return SYMNMF_OK;
 }
 
@@ -581,7 +568,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
   while (done < nsweeps) {
     const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
     TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_part,
-                   h->eng_fin, h->obj_ring, OBJ_RING, h->eng_G, h->eng_bar, h->err, h->st));
+                   h->eng_fin, h->obj_ring, OBJ_RING, h->eng_G, h->eng_bar, h->err, h->o.lai_mode != 2, h->st));
     if (obj_host) {
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
                           h->st));
@@ -602,7 +589,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
 extern "C" symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, double* obj_host) {
   if (!h || nsweeps < 0) return SYMNMF_EINVAL;
   TRYS(validate_sweep(h, source, rule));
-  if (source == SYMNMF_SRC_LAI && rule == SYMNMF_RULE_HALS && h->o.lai_mode == 0)
+  if (source == SYMNMF_SRC_LAI && rule == SYMNMF_RULE_HALS && h->o.lai_mode != 1)
     return lai_engine_sweeps(h, nsweeps, obj_host);
   int done = 0;
   bool warmed = false;

@@ -71,6 +71,8 @@ struct symnmf_ctx {
   float *Sm_f = nullptr, *Rl_f = nullptr;
   double *eng_part = nullptr, *eng_fin = nullptr, *eng_G = nullptr;  // LAI engine buffers
   unsigned* eng_bar = nullptr;
+  double *cq_part = nullptr, *cq_fin = nullptr;  // CholeskyQR engine buffers
+  float *cq_Rf = nullptr, *cq_rinv = nullptr;
 
   // LvS
   symnmf::SampleBufs sb{};

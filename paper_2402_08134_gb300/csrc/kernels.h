@@ -144,12 +144,23 @@ cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, ui
                           uint32_t iter, uint32_t side, cudaStream_t st);
 
 // ------------------------------------------------------------- LAI engine
-// All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu).
+// All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu);
+// `allow_resident` lets the CTAs keep their rows in shared memory when they fit.
 size_t lai_engine_part_doubles(int l, int k);
 size_t lai_engine_fin_doubles(int l, int k);
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, double* part, double* fin, double* obj,
-                       int obj_cap, double* Gout, unsigned* bar, unsigned* err, cudaStream_t st);
+                       int obj_cap, double* Gout, unsigned* bar, unsigned* err, bool allow_resident,
+                       cudaStream_t st);
+
+// -------------------------------------------------------------- CholeskyQR3
+// Shifted CholeskyQR3 of S (n x l, l <= 128) in place; T is n x l scratch for
+// the multi-kernel form (see cholqr.cu).  part: cholqr_part_doubles(l);
+// fin, G: l * l doubles; Rf: l * (l + 3) floats; rinv: l + 3 floats.
+size_t cholqr_part_doubles(int l);
+cudaError_t cholqr3(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G, float* Rf,
+                    float* rinv, double* ws, unsigned* counter, unsigned* bar, unsigned* err, bool allow_engine,
+                    cudaStream_t st);
 
 // -------------------------------------------------------------------- BPP
 cudaError_t bpp_rows(float* F_upd, const float* F_fix, int64_t n, int k, const double* G,

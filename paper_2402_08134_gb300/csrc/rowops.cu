@@ -26,36 +26,65 @@ __device__ bool last_block(unsigned* counter) {
   return am_last;
 }
 
-__device__ __forceinline__ double load_x(int fmt, const void* x, int64_t ldx, const float* rs,
-                                         int64_t i, int64_t j) {
-  switch (fmt) {
-    case 0: return ((const double*)x)[i * ldx + j];
-    case 1: return (double)((const float*)x)[i * ldx + j];
-    case 2: return (double)__bfloat162float(((const __nv_bfloat16*)x)[i * ldx + j]);
-    case 3: {
-      __nv_fp8_e4m3 v;
-      v.__x = ((const uint8_t*)x)[i * ldx + j];
-      return (double)rs[i] * (double)float(v);
-    }
+// Element (i, j) of dense X in its storage format, as float (FP8: times the row scale).
+template <int FMT>
+__device__ __forceinline__ float load_xf(const void* x, int64_t ldx, float rsi, int64_t i, int64_t j) {
+  if constexpr (FMT == 1) return __ldg((const float*)x + i * ldx + j);
+  if constexpr (FMT == 2) return __bfloat162float(((const __nv_bfloat16*)x)[i * ldx + j]);
+  if constexpr (FMT == 3) {
+    __nv_fp8_e4m3 v;
+    v.__x = ((const uint8_t*)x)[i * ldx + j];
+    return rsi * float(v);
   }
-  return 0.0;
+  return 0.f;
 }
 
-__global__ void xstats_dense_kernel(int fmt, const void* x, int64_t ldx, const float* rs, int64_t n,
-                                    double* out, double* ws, unsigned* counter) {
+// Kahan step: (s, c) holds the running sum s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// max, sum and sum of squares of X.  A block per row (strided), threads along
+// the row.  ||X||^2 enters the trace-trick objective, which cancels terms of
+// its size, so the sums must be accurate: FP64 input is summed in FP64; the
+// narrow formats are summed per thread and row in compensated FP32 (Kahan,
+// squares split exactly as v*v = p + e with one FMA) and only the per-row
+// results in FP64 -- FP64 arithmetic is scarce on this part.
+template <int FMT>
+__global__ void xstats_dense_kernel(const void* x, int64_t ldx, const float* rs, int64_t n, double* out,
+                                    double* ws, unsigned* counter) {
   __shared__ double sh[32];
   double mx = -INFINITY, sm = 0.0, sq = 0.0;
-  // a block per row (strided), threads along the row: no index division; FP64 sums
-  // (||X||^2 enters the trace-trick objective, which cancels terms of its size)
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      const double v = load_x(fmt, x, ldx, rs, i, j);
-      mx = fmax(mx, v);
-      sm += v;
-      sq += v * v;
+    if constexpr (FMT == 0) {
+      const double* xr = (const double*)x + i * ldx;
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = xr[j];
+        mx = fmax(mx, v);
+        sm += v;
+        sq += v * v;
+      }
+    } else {
+      const float rsi = (FMT == 3) ? rs[i] : 1.f;
+      float m = -INFINITY, s = 0.f, cs = 0.f, q = 0.f, cq = 0.f, eq = 0.f;
+#pragma unroll 8
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const float v = load_xf<FMT>(x, ldx, rsi, i, j);
+        m = fmaxf(m, v);
+        kahan_add(s, cs, v);
+        const float p = v * v;
+        eq += fmaf(v, v, -p);
+        kahan_add(q, cq, p);
+      }
+      mx = fmax(mx, (double)m);
+      sm += (double)s - (double)cs;
+      sq += ((double)q - (double)cq) + (double)eq;
     }
   }
-  // block reductions (max via negation trick is not needed: use warp_max)
+  // block reductions
   mx = warp_max(mx);
   __shared__ double shm[32];
   if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
@@ -136,8 +165,14 @@ cudaError_t xstats(int fmt, const void* x, int64_t ldx, const float* row_scale, 
   const int grid = num_sms() * 4;
   if (fmt == 4)
     xstats_csr_kernel<<<grid, 256, 0, st>>>((const float*)x, nnz, out, ws, counter);
+  else if (fmt == 0)
+    xstats_dense_kernel<0><<<grid, 256, 0, st>>>(x, ldx, row_scale, n, out, ws, counter);
+  else if (fmt == 1)
+    xstats_dense_kernel<1><<<grid, 256, 0, st>>>(x, ldx, row_scale, n, out, ws, counter);
+  else if (fmt == 2)
+    xstats_dense_kernel<2><<<grid, 256, 0, st>>>(x, ldx, row_scale, n, out, ws, counter);
   else
-    xstats_dense_kernel<<<grid, 256, 0, st>>>(fmt, x, ldx, row_scale, n, out, ws, counter);
+    xstats_dense_kernel<3><<<grid, 256, 0, st>>>(x, ldx, row_scale, n, out, ws, counter);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -7,63 +7,28 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "chol.cuh"
 #include "kernels.h"
 
 namespace symnmf {
 
-// A = G + shift I = R^T R (R upper), then Rinv = R^{-1}.  A pivot <= tol *
-// max diag is dropped (row/col of Rinv set to zero); in strict mode
+// A = G + shift I = R^T R (R upper, chol.cuh), then Rinv = R^{-1}.  A
+// dropped pivot gives a zero row/column of Rinv; in strict mode
 // (drop_tol <= 0) a pivot <= 0 also raises ERR_NOTSPD.
 __global__ void chol_inverse_kernel(const double* G, int k, double shift, double drop_tol,
                                     double* Rinv, float* Rinv_f, unsigned* err) {
   extern __shared__ double A[];  // k*k (becomes R), then X = R^{-1} k*k
   double* X = A + k * k;
   __shared__ int dropped[128];
-  __shared__ double maxdiag;
+  __shared__ double piv[256];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    A[e] = 0.5 * (G[i * k + j] + G[j * k + i]) + (i == j ? shift : 0.0);
+    A[e] = 0.5 * (G[i * k + j] + G[j * k + i]);
     X[e] = 0.0;
   }
   __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int i = 0; i < k; ++i) m = fmax(m, A[i * k + i]);
-    maxdiag = m;
-  }
-  __syncthreads();
-  // shift < 0 means a shift relative to the largest diagonal entry
-  if (shift < 0.0) {
-    for (int i = tid; i < k; i += nt) A[i * k + i] += -shift * maxdiag;
-    __syncthreads();
-  }
-  const double tol = drop_tol > 0.0 ? drop_tol * maxdiag : 0.0;
-  for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      const double d = A[j * k + j];
-      if (d <= tol || !(d > 0.0)) {
-        dropped[j] = 1;
-        A[j * k + j] = 0.0;
-        if (drop_tol <= 0.0) set_error(err, ERR_NOTSPD);
-      } else {
-        dropped[j] = 0;
-        A[j * k + j] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    const double rjj = A[j * k + j];
-    const bool dj = dropped[j];
-    for (int c = j + 1 + tid; c < k; c += nt) A[j * k + c] = dj ? 0.0 : A[j * k + c] / rjj;
-    __syncthreads();
-    // trailing update of the upper triangle
-    const int m = k - j - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int r = j + 1 + e / m, c = j + 1 + e % m;
-      if (c >= r) A[r * k + c] -= A[j * k + r] * A[j * k + c];
-    }
-    __syncthreads();
-  }
+  chol_upper_block(A, k, shift, drop_tol, piv, dropped, err);
   // R^{-1} column by column (back substitution), one column per thread
   for (int c = tid; c < k; c += nt) {
     for (int i = c; i >= 0; --i) {
@@ -87,7 +52,7 @@ __global__ void chol_inverse_kernel(const double* G, int k, double shift, double
 
 cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,
                          float* Rinv_f, unsigned* err, cudaStream_t st) {
-  if (k < 1 || k > 128) return cudaErrorInvalidValue;
+  if (k < 1 || k > 112) return cudaErrorInvalidValue;  // 2 k^2 doubles of shared memory
   const size_t smem = (size_t)2 * k * k * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

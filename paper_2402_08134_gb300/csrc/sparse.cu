@@ -1,6 +1,7 @@
 // Sparse and sampled products with X.
 //   csr_xf          : Y = X F, one warp per CSR row, each lane owning VPL
-//                     consecutive columns of F (vector loads of F rows).
+//                     consecutive columns of F (vector loads of F rows when
+//                     the rows are aligned for them, scalar loads otherwise).
 //   csr_sampled_xf  : Y += X S^T S F of Alg. LvS-SymNMF: for every sampled
 //                     row i (weight w) and nonzero (i, c, x): Y[c,:] += w x F[i,:]
 //                     (X symmetric, so sampled columns are sampled rows).
@@ -12,7 +13,7 @@
 
 namespace symnmf {
 
-template <int VPL>
+template <int VPL, bool VEC>
 __global__ void __launch_bounds__(256) csr_xf_kernel(const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col,
                                                      const float* __restrict__ val, int64_t n,
@@ -40,13 +41,13 @@ __global__ void __launch_bounds__(256) csr_xf_kernel(const int64_t* __restrict__
         const int c = __shfl_sync(0xffffffffu, cc, t);
         const float x = __shfl_sync(0xffffffffu, xv, t);
         const float* fr = F + (int64_t)c * ldf;
-        if (VPL == 4 && c0 + 3 < N) {
+        if (VEC && VPL == 4 && c0 + 3 < N) {
           const float4 f = __ldg((const float4*)(fr + c0));
           acc[0] = fmaf(x, f.x, acc[0]);
           acc[1] = fmaf(x, f.y, acc[1]);
           acc[2] = fmaf(x, f.z, acc[2]);
           acc[3] = fmaf(x, f.w, acc[3]);
-        } else if (VPL == 2 && c0 + 1 < N) {
+        } else if (VEC && VPL == 2 && c0 + 1 < N) {
           const float2 f = __ldg((const float2*)(fr + c0));
           acc[0] = fmaf(x, f.x, acc[0]);
           acc[1] = fmaf(x, f.y, acc[1]);
@@ -69,13 +70,18 @@ cudaError_t csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val,
   const int64_t warps = n;
   int grid = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (grid < 1) grid = 1;
-  const bool vec_ok = (ldf % 4 == 0) && (((uintptr_t)F & 15) == 0);
+  const bool vec4 = (ldf % 4 == 0) && (((uintptr_t)F & 15) == 0);
+  const bool vec2 = (ldf % 2 == 0) && (((uintptr_t)F & 7) == 0);
   if (N <= 32)
-    csr_xf_kernel<1><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
-  else if (N <= 64 && (ldf % 2 == 0) && (((uintptr_t)F & 7) == 0))
-    csr_xf_kernel<2><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
-  else if (N <= 128 && vec_ok)
-    csr_xf_kernel<4><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+    csr_xf_kernel<1, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+  else if (N <= 64 && vec2)
+    csr_xf_kernel<2, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+  else if (N <= 64)
+    csr_xf_kernel<2, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+  else if (N <= 128 && vec4)
+    csr_xf_kernel<4, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+  else if (N <= 128)
+    csr_xf_kernel<4, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
   else
     return cudaErrorInvalidValue;
   count_launches(1);

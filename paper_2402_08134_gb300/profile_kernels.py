@@ -2,6 +2,8 @@
 
     python -m paper_2402_08134_gb300.profile_kernels xf_tc --n 16384 --width 50
     python -m paper_2402_08134_gb300.profile_kernels lai_engine --n 20000 --k 20 --l 50 --sweeps 10
+    python -m paper_2402_08134_gb300.profile_kernels lai_engine_u --n 50000 --k 32 --l 74 --sweeps 10
+    python -m paper_2402_08134_gb300.profile_kernels sketch_u --n 50000 --l 74
     python -m paper_2402_08134_gb300.profile_kernels csr_sweep --n 200000 --k 64
     python -m paper_2402_08134_gb300.profile_kernels lvs --n 200000 --k 64
     python -m paper_2402_08134_gb300.profile_kernels batched --nprob 16
@@ -25,7 +27,7 @@ if ROOT not in sys.path:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["xf_tc", "xf_fp8", "xf_simt", "lai_engine", "lai_kernels", "full_sweep",
-                                     "csr_sweep", "lvs", "batched", "mlp"])
+                                     "lai_engine_u", "sketch_u", "csr_sweep", "lvs", "batched", "mlp"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--k", type=int, default=20)
     ap.add_argument("--l", type=int, default=50)
@@ -69,6 +71,23 @@ def main(argv=None):
         if a.case == "full_sweep":
             run = lambda: s.sweep(a.sweeps, source=S.SRC_X, record=False)  # noqa: E731
         else:
+            run = lambda: s.sweep(a.sweeps, source=S.SRC_LAI, record=False)  # noqa: E731
+    elif a.case in ("lai_engine_u", "sketch_u"):
+        # the sweeps and the range finder's orthonormalisation on a tiny identity X (CSR): a random
+        # orthonormal U (given through set_lai) for the sweeps, X Omega = Omega for the sketch
+        rp = torch.arange(n + 1, device=dev, dtype=torch.int64)
+        col = torch.arange(n, device=dev, dtype=torch.int32)
+        val = torch.ones(n, device=dev, dtype=torch.float32)
+        s = S.Solver(csr=(rp, col, val), k=a.k, n=n, max_width=a.l, seed=1, use_graph=False, alpha=1.0)
+        if a.case == "sketch_u":
+            run = lambda: s.lai_sketch(a.l, 2)  # noqa: E731
+        else:
+            import numpy as np
+
+            Q, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((n, a.l)))
+            lam = [50.0 * 0.9 ** i for i in range(a.l)]
+            s.set_lai(torch.tensor(Q, dtype=torch.float32, device=dev), lam)
+            s.set_factors(torch.rand((n, a.k), device=dev, generator=g) * 0.1)
             run = lambda: s.sweep(a.sweeps, source=S.SRC_LAI, record=False)  # noqa: E731
     elif a.case in ("csr_sweep", "lvs"):
         from synth import lvs_sample_count, sbm_csr

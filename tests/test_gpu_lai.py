@@ -17,11 +17,12 @@ def _gmm_kernel(n, d, c, seed):
     return kernel_matrix_numpy(pts, median_pair_distance(pts, seed=seed)), labels
 
 
-def test_lai_operator_matches_oracle(S):
+@pytest.mark.parametrize("lai_mode", [0, 1])  # one-launch CholeskyQR3, separate kernels per pass
+def test_lai_operator_matches_oracle(S, lai_mode):
     X, _ = _gmm_kernel(2000, 10, 8, seed=0)
     l, q, k = 30, 2, 10
     Om = gaussian_sketch(2000, l, seed=1)
-    s = S.Solver(t32(X), k, max_width=l)
+    s = S.Solver(t32(X), k, max_width=l, lai_mode=lai_mode)
     s.lai_sketch(l, q, t32(Om))
     U, lam = s.lai()
     Ug = np64(U)
@@ -34,10 +35,11 @@ def test_lai_operator_matches_oracle(S):
     np.testing.assert_allclose(np.sort(lam), np.sort(lo), rtol=1e-4, atol=1e-5 * np.abs(lo).max())
 
 
-def test_exact_range_capture_rank_deficient(S):
-    # planted X of rank 8 < l = 26: the rank-safe CholeskyQR2 keeps the captured range
+@pytest.mark.parametrize("lai_mode", [0, 1])
+def test_exact_range_capture_rank_deficient(S, lai_mode):
+    # planted X of rank 8 < l = 26: the rank-safe CholeskyQR3 keeps the captured range
     X, _, _ = planted_dense(n=800, k=8, sigma=0.0, seed=3)
-    s = S.Solver(t64(X), 8, max_width=26)
+    s = S.Solver(t64(X), 8, max_width=26, lai_mode=lai_mode)
     s.lai_sketch(26, 1)
     U, lam = s.lai()
     Ug = np64(U)
@@ -124,7 +126,7 @@ def test_lai_engine_and_per_kernel_path_match_oracle(S, n, k, l):
     alpha = 1.0
     _, Href, ref = O.lai_symnmf(Uf, lam, Hi.astype(np.float32).astype(np.float64), alpha, 30)
     Xdummy = torch.zeros((n, n), dtype=torch.float32, device="cuda")
-    for mode in (0, 1):
+    for mode in (0, 1, 2):  # resident engine, per-kernel path, streamed engine
         s = S.Solver(Xdummy, k, max_width=l, lai_mode=mode, alpha=alpha)
         s.set_lai(t32(Q), lam)
         s.set_factors(t32(Hi))
