@@ -102,7 +102,8 @@ typedef struct {
 typedef struct {
   int32_t gemm;       /* SYMNMF_GEMM_* */
   int32_t use_graph;  /* 1: record sweep bodies as CUDA graphs once and replay them */
-  int32_t max_width;  /* largest sketch width l to be requested (0: 2k + 10); <= 128 */
+  int32_t max_width;  /* largest sketch width l to be requested (0: 2k + 10); values
+                         above 96 are lowered to 96 */
   int32_t max_samples;/* largest sample count s for LvS calls (0: n) */
   int32_t lai_mode;   /* LAI steps: 0 = persistent cooperative launches (all
                          LAI-HALS sweeps in one, each CholeskyQR3 of the range

@@ -407,10 +407,9 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
   TRY(dalloc(h, &h->ev, (size_t)L));
   TRY(dalloc(h, &h->Sm_f, (size_t)L * L));
   TRY(dalloc(h, &h->Rl_f, (size_t)L * L));
-  TRY(dalloc(h, &h->eng_part, lai_engine_part_doubles(L, h->k)));
-  TRY(dalloc(h, &h->eng_fin, lai_engine_fin_doubles(L, h->k)));
+  TRY(dalloc(h, &h->eng_ws, lai_engine_ws_bytes(L, h->k, OBJ_RING)));
   TRY(dalloc(h, &h->eng_G, (size_t)2 * h->k * h->k));
-  TRY(dalloc(h, &h->eng_bar, 64));  // counter and generation in separate 128-byte lines
+  TRY(dalloc(h, &h->eng_bar, 64));  // barrier counter of the CholeskyQR3 launch
   TRY(dalloc(h, &h->cq_part, cholqr_part_doubles(L)));
   TRY(dalloc(h, &h->cq_fin, (size_t)L * L));
   TRY(dalloc(h, &h->cq_Rf, (size_t)L * (L + 3)));
@@ -567,8 +566,8 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
   int done = 0;
   while (done < nsweeps) {
     const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
-    TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_part,
-                   h->eng_fin, h->obj_ring, OBJ_RING, h->eng_G, h->eng_bar, h->err, h->o.lai_mode != 2, h->st));
+    TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
+                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st));
     if (obj_host) {
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
                           h->st));

@@ -3,8 +3,9 @@
 // Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020).
 // Pass 1 factors Y^T Y + 1e-6 max_i (Y^T Y)_ii I, which is positive definite
 // whatever the rank of Y; passes 2 and 3 are plain CholeskyQR.  Each pass:
-// G = Y^T Y (FP64 sum of compensated FP32 partials), G + sI = R^T R in FP64
-// (chol.cuh), then every row y of Y becomes the solution x of x R = y
+// G = Y^T Y (compensated FP32 partials summed in double-float), G + sI = R^T R
+// in double-float (chol.cuh, dfloat.cuh: GB300's FP64 rate is a small fraction
+// of its FP32 rate), then every row y of Y becomes the solution x of x R = y
 // (forward substitution in FP32).  Pivots below 1e-12 (pass 1) or 1e-10
 // (passes 2, 3) of the largest diagonal entry are dropped -- a zero column of
 // Q -- so a rank-deficient sketch keeps exactly its numerical range.
@@ -23,6 +24,7 @@
 
 #include "chol.cuh"
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "persist.cuh"
 
@@ -62,14 +64,14 @@ __device__ __forceinline__ void cq_solve_row(float (&s)[LMAX], const float* Rf, 
   }
 }
 
-// R (FP64, upper, in A) -> Rf (FP32 strictly upper, l x l4) and rinv (l4).
-__device__ __forceinline__ void cq_pack_r(const double* A, const int* dropped, int l, int l4, float* Rf,
-                                          float* rinv) {
+// R (double-float, upper, in A) -> Rf (FP32 strictly upper, l x l4) and rinv (l4).
+__device__ __forceinline__ void cq_pack_r(const dfl* A, const int* dropped, int l, int l4, float* Rf, float* rinv) {
   for (int e = threadIdx.x; e < l * l4; e += blockDim.x) {
     const int i = e / l4, j = e - i * l4;
-    Rf[e] = (j > i && j < l) ? (float)A[i * l + j] : 0.f;
+    Rf[e] = (j > i && j < l) ? A[i * l + j].hi + A[i * l + j].lo : 0.f;
   }
-  for (int i = threadIdx.x; i < l4; i += blockDim.x) rinv[i] = (i < l && !dropped[i]) ? (float)(1.0 / A[i * l + i]) : 0.f;
+  for (int i = threadIdx.x; i < l4; i += blockDim.x)
+    rinv[i] = (i < l && !dropped[i]) ? 1.0f / (A[i * l + i].hi + A[i * l + i].lo) : 0.f;
 }
 
 __host__ __device__ inline int cq_tiles(int l) {
@@ -93,40 +95,61 @@ struct CqArgs {
   int64_t n;
   int l;
   int rp;          // padded rows per CTA (multiple of 4)
-  double* part;    // [grid * RG][l * l] partial Grams
-  double* fin;     // [l * l]
-  unsigned* bar;   // 2 * GRID_GEN words, zeroed
+  int pitch;       // column pitch of Y in shared memory (rp padded to 8, plus 32)
+  dfl* part;       // [grid * RG][l * l] partial Grams
+  dfl* fin;        // [l * l]
+  unsigned* bar;   // barrier counter, zeroed
   unsigned* err;
 };
 
+constexpr int CQ_BATCH = 16;
+
 __host__ __device__ inline size_t cq_engine_smem(int l, int rp) {
   const int l4 = (l + 3) & ~3;
-  size_t b = (size_t)l * l * 8 + (size_t)2 * l * 8;  // A, piv
+  size_t b = (size_t)l * l * 8 + (size_t)2 * l * 8;  // A, piv, 1 / pivot (double-float)
   b = (b + 15) & ~(size_t)15;
-  b += (size_t)l4 * rp * 4;                           // Yt
+  b += (size_t)CQ_THREADS * 8;                         // reduction partials (double-float)
+  b += (size_t)l4 * (((rp + 7) & ~7) + 32) * 4;       // Yt (skewed columns)
   b += (size_t)l * l4 * 4 + (size_t)l4 * 4;            // Rf, rinv
   b += (size_t)l * 4 + (size_t)cq_tiles(l) * 4;        // dropped, tile table
+  b += (size_t)l * (l + 1) / 2 * 4;                    // triangle entries of the Cholesky
   return b;
+}
+
+// Double-float sum of N values by a balanced tree (depth log2 N).
+template <int N>
+__device__ __forceinline__ dfl cq_tree_sum(dfl (&v)[N]) {
+#pragma unroll
+  for (int w = N / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int u = 0; u < w; ++u) v[u] = df_add(v[u], v[u + w]);
+  return v[0];
 }
 
 template <int LMAX>
 __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int l = a.l, l4 = (l + 3) & ~3, RP = a.rp, E = l * l;
-  double* A = reinterpret_cast<double*>(smraw);  // l x l
-  double* piv = A + l * l;                        // 2 l
-  float* Yt = reinterpret_cast<float*>(smraw + (((size_t)l * l * 8 + (size_t)2 * l * 8 + 15) & ~(size_t)15));
-  float* Rf = Yt + l4 * RP;                       // l x l4
+  const int l = a.l, l4 = (l + 3) & ~3, RP = a.rp, P = a.pitch, E = l * l;
+  // column c of Y starts at c P + 4 ((c / 4) mod 8): the 4-column blocks read
+  // together by the Gram tiles fall in different bank groups
+  auto col = [P](int c) { return c * P + ((c >> 2) & 7) * 4; };
+  dfl* A = reinterpret_cast<dfl*>(smraw);        // l x l
+  dfl* piv = A + l * l;                           // l
+  dfl* invd = piv + l;                            // l
+  dfl* red = reinterpret_cast<dfl*>(smraw + (((size_t)l * l * 8 + (size_t)2 * l * 8 + 15) & ~(size_t)15));
+  float* Yt = reinterpret_cast<float*>(red + CQ_THREADS);
+  float* Rf = Yt + l4 * P;                        // l x l4
   float* rinv = Rf + l * l4;                      // l4
   int* dropped = reinterpret_cast<int*>(rinv + l4);
   int* tiles = dropped + l;                       // (bi << 16) | bj, bi <= bj
+  ushort2* tri = reinterpret_cast<ushort2*>(tiles + cq_tiles(l));
 
   const int tid = threadIdx.x;
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
   const int R = (int)((a.n * (blockIdx.x + 1)) / gridDim.x - r0);
   const int nb = l4 / 4, T = cq_tiles(l), RG = cq_row_groups(l);
 
-  for (int e = tid; e < l4 * RP; e += CQ_THREADS) Yt[e] = 0.f;
+  for (int e = tid; e < l4 * P; e += CQ_THREADS) Yt[e] = 0.f;
   if (tid == 0) {
     int t = 0;
     for (int bi = 0; bi < nb; ++bi)
@@ -137,27 +160,34 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
     const float* Sg = a.S + r0 * l;
     for (int e = tid; e < R * l; e += CQ_THREADS) {
       const int r = e / l, c = e - r * l;
-      Yt[c * RP + r] = Sg[e];
+      Yt[col(c) + r] = Sg[e];
     }
   }
   __syncthreads();
 
+  unsigned epoch = 0;
   for (int pass = 0; pass < 3; ++pass) {
     // partial Gram of this CTA's rows: 4x4 upper tiles, four rows per float4 step
     for (int w = tid; w < T * RG; w += CQ_THREADS) {
       const int tile = w % T, rg = w / T;
       const int bi = tiles[tile] >> 16, bj = tiles[tile] & 0xffff;
-      const float* Ab = Yt + 4 * bi * RP;
-      const float* Bb = Yt + 4 * bj * RP;
+      const float4* Ap[4];
+      const float4* Bp[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        Ap[p] = reinterpret_cast<const float4*>(Yt + col(4 * bi + p));
+        Bp[p] = reinterpret_cast<const float4*>(Yt + col(4 * bj + p));
+      }
       float acc[16], cmp[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[e] = cmp[e] = 0.f;
+#pragma unroll 1
       for (int c = rg; c < RP / 4; c += RG) {
         float4 av[4], bv[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-          av[p] = reinterpret_cast<const float4*>(Ab + p * RP)[c];
-          bv[p] = reinterpret_cast<const float4*>(Bb + p * RP)[c];
+          av[p] = Ap[p][c];
+          bv[p] = Bp[p][c];
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p)
@@ -170,51 +200,74 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
             cq_kahan(acc[p * 4 + q], cmp[p * 4 + q], v);
           }
       }
-      double* rec = a.part + ((size_t)blockIdx.x * RG + rg) * E;
+      dfl* rec = a.part + ((size_t)blockIdx.x * RG + rg) * E;
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int i = 4 * bi + (e >> 2), j = 4 * bj + (e & 3);
         if (i < l && j < l) {
-          const double v = (double)acc[e] - (double)cmp[e];
+          const dfl v{acc[e], -cmp[e]};  // Kahan pair: sum = acc - cmp
           rec[i * l + j] = v;
           rec[j * l + i] = v;
         }
       }
     }
-    if (!grid_sync_bounded(a.bar, a.err)) return;
-    // sliced fixed-order reduction of the grid * RG records into fin
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+    // sliced fixed-order reduction of the grid * RG records into fin: CTA c
+    // owns a contiguous run of entries, read coalesced (consecutive threads,
+    // consecutive entries of one record); each thread sums every S-th record,
+    // and the S partial sums of an entry are added in a fixed order
     {
       const unsigned nrec = gridDim.x * RG;
       const int per = (E + gridDim.x - 1) / gridDim.x;
-      const int e0 = blockIdx.x * per, e1 = min(E, e0 + per);
-      const int grp = tid >> 4, sub = tid & 15;
-      for (int base = e0; base < e1; base += CQ_THREADS / 16) {
-        const int e = base + grp;
-        double s = 0.0;
-        if (e < e1) {
-#pragma unroll 4
-          for (unsigned q = sub; q < nrec; q += 16) s += __ldcg(a.part + (size_t)q * E + e);
-        }
+      const int c0 = blockIdx.x * per, c1 = min(E, c0 + per);
+      for (int i0 = c0; i0 < c1; i0 += CQ_THREADS) {
+        const int np = min(CQ_THREADS, c1 - i0), S = CQ_THREADS / np;
+        const int pos = tid % np, g = tid / np;
+        if (g < S) {
+          dfl acc{0.f, 0.f};
+          for (unsigned q0 = g; q0 < nrec; q0 += (unsigned)S * CQ_BATCH) {
+            dfl v[CQ_BATCH];
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (e < e1 && sub == 0) a.fin[e] = s;
+            for (int u = 0; u < CQ_BATCH; ++u) {
+              const unsigned q = q0 + (unsigned)S * u;
+              if (q < nrec) {
+                const float2 f = __ldcg(reinterpret_cast<const float2*>(a.part + (size_t)q * E + i0 + pos));
+                v[u] = dfl{f.x, f.y};
+              } else {
+                v[u] = dfl{0.f, 0.f};
+              }
+            }
+            acc = df_add(acc, cq_tree_sum<CQ_BATCH>(v));
+          }
+          red[g * np + pos] = acc;
+        }
+        __syncthreads();
+        if (tid < np) {
+          dfl s{0.f, 0.f};
+          for (int gg = 0; gg < S; ++gg) s = df_add(s, red[gg * np + tid]);
+          a.fin[i0 + tid] = s;
+        }
+        __syncthreads();
       }
     }
-    if (!grid_sync_bounded(a.bar, a.err)) return;
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
 #pragma unroll 4
-    for (int e = tid; e < E; e += CQ_THREADS) A[e] = __ldcg(a.fin + e);
+    for (int e = tid; e < E; e += CQ_THREADS) {
+      const float2 f = __ldcg(reinterpret_cast<const float2*>(a.fin + e));
+      A[e] = dfl{f.x, f.y};
+    }
     __syncthreads();
-    chol_upper_block(A, l, cq_shift(pass), cq_drop(pass), piv, dropped, blockIdx.x == 0 ? a.err : nullptr);
+    chol_upper_block_df(A, l, cq_shift(pass), cq_drop(pass), piv, invd, dropped, tri);
     cq_pack_r(A, dropped, l, l4, Rf, rinv);
     __syncthreads();
     for (int r = tid; r < R; r += CQ_THREADS) {
       float s[LMAX];
 #pragma unroll
-      for (int j = 0; j < LMAX; ++j) s[j] = j < l ? Yt[j * RP + r] : 0.f;
+      for (int j = 0; j < LMAX; ++j) s[j] = j < l ? Yt[col(j) + r] : 0.f;
       cq_solve_row<LMAX>(s, Rf, rinv, l, l4);
 #pragma unroll
       for (int j = 0; j < LMAX; ++j)
-        if (j < l) Yt[j * RP + r] = s[j];
+        if (j < l) Yt[col(j) + r] = s[j];
     }
     __syncthreads();
   }
@@ -222,25 +275,24 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
     float* Sg = a.S + r0 * l;
     for (int e = tid; e < R * l; e += CQ_THREADS) {
       const int r = e / l, c = e - r * l;
-      Sg[e] = Yt[c * RP + r];
+      Sg[e] = Yt[col(c) + r];
     }
   }
 }
 
 // ------------------------------------------------------ multi-kernel passes
 
-__global__ void chol_factor_kernel(const double* G, int l, double shift, double drop_tol, float* Rf, float* rinv,
-                                   unsigned* err) {
-  extern __shared__ __align__(16) double Ash[];  // l x l
-  __shared__ double piv[256];
+__global__ void chol_factor_kernel(const double* G, int l, double shift, double drop_tol, float* Rf, float* rinv) {
+  extern __shared__ __align__(16) dfl Ash[];  // l x l, then the triangle entries
+  __shared__ dfl piv[128], invd[128];
   __shared__ int dropped[128];
   const int l4 = (l + 3) & ~3;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e - i * l;
-    Ash[e] = 0.5 * (G[i * l + j] + G[j * l + i]);
+    Ash[e] = df_from_double(0.5 * (G[i * l + j] + G[j * l + i]));
   }
   __syncthreads();
-  chol_upper_block(Ash, l, shift, drop_tol, piv, dropped, err);
+  chol_upper_block_df(Ash, l, shift, drop_tol, piv, invd, dropped, reinterpret_cast<ushort2*>(Ash + l * l));
   cq_pack_r(Ash, dropped, l, l4, Rf, rinv);
 }
 
@@ -288,9 +340,11 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cholqr_engine_kernel<LMAX>, CQ_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (per_sm >= 1) {
-      e = cudaMemsetAsync(bar, 0, 2 * GRID_GEN * sizeof(unsigned), st);
+      e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
       if (e != cudaSuccess) return e;
-      CqArgs a{S, n, l, (int)rp, part, fin, bar, err};
+      // the double-typed buffers hold double-float pairs (same size)
+      CqArgs a{S, n, l, (int)rp, (int)(((rp + 7) & ~7LL) + 32), reinterpret_cast<dfl*>(part),
+               reinterpret_cast<dfl*>(fin), bar, err};
       void* params[] = {&a};
       e = cudaLaunchCooperativeKernel((const void*)cholqr_engine_kernel<LMAX>, dim3(grid), dim3(CQ_THREADS),
                                       params, smem, st);
@@ -302,7 +356,7 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
   float* src = S;
   float* dst = T;
   const int l4 = (l + 3) & ~3;
-  const size_t fsmem = (size_t)l * l * 8;
+  const size_t fsmem = (size_t)l * l * 8 + (size_t)l * (l + 1) / 2 * 4;
   e = cudaFuncSetAttribute(chol_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
   if (e != cudaSuccess) return e;
   const size_t tsmem = (size_t)(l * l4 + l4) * 4;
@@ -311,7 +365,7 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
   for (int pass = 0; pass < 3; ++pass) {
     e = xcross(src, l, l, src, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, counter, st);
     if (e != cudaSuccess) return e;
-    chol_factor_kernel<<<1, 256, fsmem, st>>>(G, l, cq_shift(pass), cq_drop(pass), Rf, rinv, err);
+    chol_factor_kernel<<<1, 256, fsmem, st>>>(G, l, cq_shift(pass), cq_drop(pass), Rf, rinv);
     trsm_rows_kernel<LMAX><<<(unsigned)((n + 127) / 128), 128, tsmem, st>>>(src, n, l, Rf, rinv, dst);
     count_launches(2);
     e = cudaGetLastError();
@@ -325,14 +379,14 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
 cudaError_t cholqr3(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G, float* Rf,
                     float* rinv, double* ws, unsigned* counter, unsigned* bar, unsigned* err, bool allow_engine,
                     cudaStream_t st) {
-  if (n < 1 || l < 1 || l > 128) return cudaErrorInvalidValue;
+  if (n < 1 || l < 1 || l > 96) return cudaErrorInvalidValue;
   if (l <= 32)
     return cholqr_run<32>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
   if (l <= 64)
     return cholqr_run<64>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
-  if (l <= 96)
-    return cholqr_run<96>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
-  return cholqr_run<128>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+  if (l <= 80)
+    return cholqr_run<80>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+  return cholqr_run<96>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
 }
 
 }  // namespace symnmf

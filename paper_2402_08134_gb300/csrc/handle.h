@@ -69,7 +69,8 @@ struct symnmf_ctx {
   float *Om = nullptr, *Qa = nullptr, *Qb = nullptr, *U = nullptr, *Mf = nullptr;
   double *Sm_d = nullptr, *V_d = nullptr, *lam = nullptr, *ev = nullptr;
   float *Sm_f = nullptr, *Rl_f = nullptr;
-  double *eng_part = nullptr, *eng_fin = nullptr, *eng_G = nullptr;  // LAI engine buffers
+  char* eng_ws = nullptr;    // LAI engine workspace
+  double* eng_G = nullptr;   // Grams after the engine's last sweep
   unsigned* eng_bar = nullptr;
   double *cq_part = nullptr, *cq_fin = nullptr;  // CholeskyQR engine buffers
   float *cq_Rf = nullptr, *cq_rinv = nullptr;

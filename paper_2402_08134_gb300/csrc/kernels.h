@@ -108,7 +108,7 @@ cudaError_t check_factor(const float* F, int64_t count, unsigned* flags, cudaStr
 cudaError_t normalize_rows(const float* in, int64_t n, int l, float* out, cudaStream_t st);
 
 // --------------------------------------------------------- small FP64 dense
-// Cholesky of G + shift I (k <= 128): R upper, Rinv (FP64 and FP32 copies).
+// Cholesky of G + shift I (k <= 112): R upper, Rinv (FP64 and FP32 copies).
 // drop_tol > 0: pivots <= drop_tol * max_diag give zero rows/cols in Rinv
 // (rank-safe mode); else such a pivot sets ERR_NOTSPD.
 cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,
@@ -146,15 +146,13 @@ cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, ui
 // ------------------------------------------------------------- LAI engine
 // All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu);
 // `allow_resident` lets the CTAs keep their rows in shared memory when they fit.
-size_t lai_engine_part_doubles(int l, int k);
-size_t lai_engine_fin_doubles(int l, int k);
+size_t lai_engine_ws_bytes(int l, int k, int obj_cap);
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
-                       int nsweeps, double alpha, const double* normX2, double* part, double* fin, double* obj,
-                       int obj_cap, double* Gout, unsigned* bar, unsigned* err, bool allow_resident,
-                       cudaStream_t st);
+                       int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
+                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st);
 
 // -------------------------------------------------------------- CholeskyQR3
-// Shifted CholeskyQR3 of S (n x l, l <= 128) in place; T is n x l scratch for
+// Shifted CholeskyQR3 of S (n x l, l <= 96) in place; T is n x l scratch for
 // the multi-kernel form (see cholqr.cu).  part: cholqr_part_doubles(l);
 // fin, G: l * l doubles; Rf: l * (l + 3) floats; rinv: l + 3 floats.
 size_t cholqr_part_doubles(int l);

@@ -10,26 +10,35 @@
 // owns the contiguous rows [n c / grid, n (c + 1) / grid) of U, W and H.
 //
 //   per half sweep
-//     1. each CTA updates its rows (Y_r = U_r M in registers; columns in
-//        order, each using the ones already updated) and accumulates, over its
-//        rows, FP32 partials of U^T F_upd, F_upd^T F_upd, and FP64 sums of
-//        per-row F_upd . Y and ||F_upd - F_fix||^2;
+//     1. each CTA updates its rows (Y = U M for its rows, then per row the
+//        columns in order, each using the ones already updated) and writes
+//        one FP32 record of its partial sums over its rows: U^T F_upd,
+//        F_upd^T F_upd (upper 4x4 tiles), and (as hi/lo float pairs of FP64
+//        sums) F_upd . Y and ||F_upd - F_fix||^2;
 //     2. grid barrier;
-//     3. CTA c sums slice c of the entries over all CTA partials in FP64
-//        (fixed order: deterministic) into a global "final" buffer;
+//     3. CTA c sums slice c of the entries over all records in double-float
+//        (Dekker's two-sum; fixed order: deterministic) and writes the FP64
+//        sums, plus the next half's state in FP32 -- lambda-scaled M, G and
+//        1 / (G_ii + alpha) laid out as the CTAs hold them in shared memory --
+//        and, after the H half, its share of the surrogate objective (trace
+//        trick, FP64);
 //     4. grid barrier;
-//     5. every CTA loads the new M (rows scaled by lambda) and G; CTA 0 writes
-//        the surrogate objective after the H half (trace trick, FP64).
+//     5. every CTA copies the state into shared memory (float4 loads).
+//   After the last sweep the CTAs sum the objective shares of every sweep.
 //
 // Two variants of the row work:
 //   resident  the CTA's rows of U, W and H stay in shared memory for the whole
-//             launch, stored column-major (entry (r, c) at c * RP + r, RP = the
-//             row count padded to 4): per-row reads by thread r are
-//             conflict-free and the cross-product partials read float4 runs of
-//             four rows.  W and H reach global memory once, at the end.  Used
-//             whenever the rows fit (n = 5e4, k = 32, l = 74 takes 216 KB).
+//             launch, stored column-major: column c starts at c P + 4 ((c / 4)
+//             mod 8), P = the row count padded to 8 plus 32, a skew that puts
+//             the four-column blocks read together by the cross products in
+//             different bank groups.  Y = U M is a CTA-wide product with 4x4
+//             register tiles into shared memory; the per-row column updates
+//             (one thread per row) read Y from there; the cross products read
+//             float4 runs of four rows.  W and H reach global memory once, at
+//             the end.  Used whenever the rows fit.
 //   streamed  rows pass through shared memory in tiles of up to 256, staged
-//             from and written back to global memory every half sweep.
+//             from and written back to global memory every half sweep; each
+//             thread forms its row of Y itself.
 //
 // The grid barrier (persist.cuh) is bounded: on expiry the host reads an
 // error status instead of a hung launch.  Co-residency of all CTAs comes
@@ -56,22 +65,90 @@ struct LaiArgs {
   float alpha;
   double alpha_d;
   const double* normX2;  // sum lambda^2
-  double* part;          // [gridDim][E]
+  float* part;           // [gridDim * RG][EP] partial records
   double* fin;           // [2][E]: final sums, slot 0 = W side, slot 1 = H side
+  float* state;          // [2][SL]: M (lambda-scaled, l x k4), G (gp x gp), 1 / (G_ii + alpha) (gp)
+  double* objp;          // [obj_cap][gridDim]: objective shares
   double* obj;           // [nsweeps] (ring, capacity cap)
   int obj_cap;
   double* Gout;          // [2][k*k] FP64 Grams after the last sweep: [0] H^T H, [1] W^T W
   unsigned* bar;
   unsigned* err;
-  int tile_rows;         // streamed: rows per tile; resident: padded rows per CTA (RP)
+  int tile_rows;         // streamed: rows per tile; resident: rows per CTA padded to 4 (RP)
+  int gp;                // G held as gp x gp (gp = KMAX of the kernel), zero padded
+  int pitch;             // resident: column pitch (RP padded to 8)
 };
 
-// Layout of one partial / final record: l*k entries of U^T F, k*k of F^T F, then tr, dd.
+// Final sums: l*k entries of U^T F, k*k of F^T F, then tr, dd.
 __host__ __device__ inline int le_entries(int l, int k) { return l * k + k * k + 2; }
+// State of a half: M (l x k4, lambda-scaled), G (gp x gp), 1 / (G_ii + alpha) (gp), zero padded.
+__host__ __device__ inline int le_state_floats(int l, int k, int gp) { return l * ((k + 3) & ~3) + gp * gp + gp; }
+__host__ __device__ inline int le_gp(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 24 ? 24 : k <= 32 ? 32 : k <= 48 ? 48 : 64; }
 
-// 4x4 tiles over [U^T F (l4/4 x k4/4 tiles) | F^T F (k4/4 x k4/4 tiles)], spread
-// over the block's threads; with fewer tiles than threads, RG row groups of
-// threads split the rows and are combined in a fixed order.
+// 4x4 tiles: (l4/4) x (k4/4) tiles of U^T F, then the upper-triangular tiles
+// (bi <= bj, row-major) of F^T F.  A partial record stores tile t's 16
+// entries at [16 t, 16 t + 16) and then tr, tr_lo, dd, dd_lo.
+__host__ __device__ inline int le_tile_count(int l, int k) {
+  const int kt = ((k + 3) & ~3) / 4, lt = ((l + 3) & ~3) / 4;
+  return lt * kt + kt * (kt + 1) / 2;
+}
+__host__ __device__ inline int le_rec_entries(int l, int k) { return 16 * le_tile_count(l, k) + 4; }
+__host__ __device__ inline int le_tri_index(int bi, int bj, int kt) { return bi * kt - bi * (bi - 1) / 2 + (bj - bi); }
+
+__device__ __forceinline__ void le_tri(int g, int kt, int& bi, int& bj) {
+  int b = 0;
+  while (g >= kt - b) {
+    g -= kt - b;
+    ++b;
+  }
+  bi = b;
+  bj = b + g;
+}
+
+// Record position of final entry e (< l*k + k*k).
+__device__ __forceinline__ int le_rec_index(int e, int l, int k) {
+  const int kt = ((k + 3) & ~3) / 4, lk = l * k;
+  if (e < lk) {
+    const int i = e / k, j = e - i * k;
+    return ((i >> 2) * kt + (j >> 2)) * 16 + (i & 3) * 4 + (j & 3);
+  }
+  const int g = e - lk, i = g / k, j = g - i * k;
+  int bi = i >> 2, bj = j >> 2, p = i & 3, q = j & 3;
+  if (bi > bj) {
+    const int t = bi;
+    bi = bj;
+    bj = t;
+    const int u = p;
+    p = q;
+    q = u;
+  }
+  const int tm = (((l + 3) & ~3) / 4) * kt;
+  return (tm + le_tri_index(bi, bj, kt)) * 16 + p * 4 + q;
+}
+
+// Double-float accumulation (Dekker 1971, two-sum): (hi, lo) holds hi + lo.
+__device__ __forceinline__ void df_add_f(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2;
+  const float bb = s - hi;
+  const float t = ((hi - (s - bb)) + (h2 - bb)) + lo + l2;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+
+// Tiles spread over the block's threads; with fewer tiles than threads, up
+// to LE_MAXRG row groups of threads split the rows, each group writing its
+// own record.
+constexpr int LE_MAXRG = 4;
+__host__ __device__ inline int le_row_groups(int l, int k) {
+  const int T = le_tile_count(l, k);
+  return T >= LE_THREADS ? 1 : (LE_THREADS / T < LE_MAXRG ? LE_THREADS / T : LE_MAXRG);
+}
 struct LeTiles {
   int kt, tm, T, RG, my_rg, TPT;
 };
@@ -80,10 +157,10 @@ __device__ __forceinline__ LeTiles le_tiles(int l4, int k4) {
   LeTiles t;
   t.kt = k4 / 4;
   t.tm = (l4 / 4) * t.kt;
-  t.T = t.tm + t.kt * t.kt;
-  t.RG = t.T >= LE_THREADS ? 1 : LE_THREADS / t.T;
+  t.T = t.tm + t.kt * (t.kt + 1) / 2;
+  t.RG = t.T >= LE_THREADS ? 1 : min(LE_MAXRG, LE_THREADS / t.T);
   t.my_rg = t.T >= LE_THREADS ? 0 : (int)threadIdx.x / t.T;
-  t.TPT = (t.T + LE_THREADS - 1) / LE_THREADS;  // <= 4 for l <= 96, k <= 64
+  t.TPT = (t.T + LE_THREADS - 1) / LE_THREADS;  // <= 3 for l <= 96, k <= 64
   return t;
 }
 
@@ -91,161 +168,226 @@ __device__ __forceinline__ int le_tile_of(const LeTiles& tl, int t) {
   return (tl.T >= LE_THREADS) ? (int)threadIdx.x + t * LE_THREADS : (int)threadIdx.x % tl.T;
 }
 
-__device__ __forceinline__ void le_clear(float (&acc)[4][16]) {
+// Operand block rows of tile `tile`: A (U columns or F columns) and B (F columns).
+__device__ __forceinline__ void le_tile_rows(const LeTiles& tl, int tile, int& a_blk, int& b_blk, bool& a_is_u) {
+  if (tile < tl.tm) {
+    a_is_u = true;
+    a_blk = tile / tl.kt;
+    b_blk = tile % tl.kt;
+  } else {
+    a_is_u = false;
+    le_tri(tile - tl.tm, tl.kt, a_blk, b_blk);
+  }
+}
+
+__device__ __forceinline__ void le_clear(float (&acc)[3][16]) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < 3; ++t)
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[t][e] = 0.f;
 }
 
-// Combine row groups (fixed order) and write this CTA's FP64 record.
-__device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, const float (&acc)[4][16],
-                                          float* red, double* shd, double tr, double dd) {
-  const int k = a.k, l = a.l, E = le_entries(l, k);
-  double* rec = a.part + (size_t)blockIdx.x * E;
+// Write this CTA's records (one per row group; coalesced float4 stores of the
+// tiles) and the CTA's tr, dd (double-float, reduced over the block with one
+// barrier) into the first record; the other records' tr, dd slots get zeros.
+__device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, const float (&acc)[3][16],
+                                          float* red, float2 trv, float2 ddv) {
+  const int EP = le_rec_entries(a.l, a.k);
+  float* rec0 = a.part + (size_t)blockIdx.x * tl.RG * EP;
   for (int t = 0; t < tl.TPT; ++t) {
     const int tile = le_tile_of(tl, t);
-    const int slot = (tile % LE_THREADS) * 16;
-    for (int g = 0; g < tl.RG; ++g) {
-      if (tile < tl.T && tl.my_rg == g) {
+    if (tile < tl.T && tl.my_rg < tl.RG) {
+      float4* rec4 = reinterpret_cast<float4*>(rec0 + (size_t)tl.my_rg * EP);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          float v = 0.f;
+      for (int u = 0; u < 4; ++u) {
+        float v[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (u == t) v = acc[u][e];
-          red[slot + e] = (g == 0 ? 0.f : red[slot + e]) + v;
+        for (int e = 0; e < 4; ++e) {
+          v[e] = 0.f;
+#pragma unroll
+          for (int w = 0; w < 3; ++w)
+            if (w == t) v[e] = acc[w][4 * u + e];
         }
+        rec4[tile * 4 + u] = make_float4(v[0], v[1], v[2], v[3]);
       }
-      __syncthreads();
     }
-    if (tile < tl.T && tl.my_rg == 0) {
+  }
+  // tr, dd: warp xor trees, then one barrier and warp 0
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int p = e >> 2, q = e & 3;
-        if (tile < tl.tm) {
-          const int i = (tile / tl.kt) * 4 + p, j = (tile % tl.kt) * 4 + q;
-          if (i < l && j < k) rec[i * k + j] = (double)red[slot + e];
+  for (int o = 16; o > 0; o >>= 1) {
+    df_add(trv.x, trv.y, __shfl_xor_sync(0xffffffffu, trv.x, o), __shfl_xor_sync(0xffffffffu, trv.y, o));
+    df_add(ddv.x, ddv.y, __shfl_xor_sync(0xffffffffu, ddv.x, o), __shfl_xor_sync(0xffffffffu, ddv.y, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[4 * wid + 0] = trv.x;
+    red[4 * wid + 1] = trv.y;
+    red[4 * wid + 2] = ddv.x;
+    red[4 * wid + 3] = ddv.y;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = LE_THREADS / 32;
+    float th = lane < nw ? red[4 * lane + 0] : 0.f, tl2 = lane < nw ? red[4 * lane + 1] : 0.f;
+    float dh = lane < nw ? red[4 * lane + 2] : 0.f, dl = lane < nw ? red[4 * lane + 3] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df_add(th, tl2, __shfl_xor_sync(0xffffffffu, th, o), __shfl_xor_sync(0xffffffffu, tl2, o));
+      df_add(dh, dl, __shfl_xor_sync(0xffffffffu, dh, o), __shfl_xor_sync(0xffffffffu, dl, o));
+    }
+    if (lane < tl.RG) {
+      float* r2 = rec0 + (size_t)lane * EP + EP - 4;
+      r2[0] = lane == 0 ? th : 0.f;
+      r2[1] = lane == 0 ? tl2 : 0.f;
+      r2[2] = lane == 0 ? dh : 0.f;
+      r2[3] = lane == 0 ? dl : 0.f;
+    }
+  }
+  __syncthreads();  // red is reused by the caller
+}
+
+// Sliced reduction of all records.  CTA c owns a contiguous run of record
+// positions; its threads read them coalesced (consecutive threads, consecutive
+// positions of one record), each thread summing every S-th record in
+// double-float, and the S partial sums of a position are then added in a fixed
+// order (deterministic).  Each position is mapped back to its entry: the FP64
+// sums go to fin[side] (both (i, j) and (j, i) for F^T F), the FP32 state of the
+// next half to state[side], and after the H half of sweep t >= 0 this CTA's
+// objective share to objp[t].
+constexpr int LE_BATCH = 32;
+
+__device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int t, float* red, double* shd) {
+  const int k = a.k, l = a.l, k4 = (k + 3) & ~3, gp = a.gp;
+  const int E = le_entries(l, k), EP = le_rec_entries(l, k), SL = le_state_floats(l, k, gp);
+  const int lk = l * k, kt = k4 / 4, tm = (((l + 3) & ~3) / 4) * kt;
+  const unsigned nrec = gridDim.x * le_row_groups(l, k);
+  double* fin = a.fin + side * E;
+  float* st = a.state + side * SL;
+  // positions per CTA, even: the hi/lo pairs of tr and dd (at EP - 4, EP - 2) never straddle two CTAs
+  const int per = ((EP + gridDim.x - 1) / gridDim.x + 1) & ~1;
+  const int c0 = blockIdx.x * per, c1 = min(EP, c0 + per);
+  double share = 0.0;
+  for (int i0 = c0; i0 < c1; i0 += LE_THREADS) {  // chunks of at most LE_THREADS positions
+    const int np = min(LE_THREADS, c1 - i0);
+    const int S = LE_THREADS / np;  // record strides
+    const int pos = threadIdx.x % np, g = threadIdx.x / np;
+    const int idx = i0 + pos;
+    float hi = 0.f, lo = 0.f;
+    if (g < S) {
+      for (unsigned q0 = g; q0 < nrec; q0 += (unsigned)S * LE_BATCH) {
+        float v[LE_BATCH];
+#pragma unroll
+        for (int u = 0; u < LE_BATCH; ++u) {
+          const unsigned q = q0 + (unsigned)S * u;
+          v[u] = q < nrec ? __ldcg(a.part + (size_t)q * EP + idx) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < LE_BATCH; ++u) df_add(hi, lo, v[u], 0.f);
+      }
+      red[2 * (g * np + pos)] = hi;
+      red[2 * (g * np + pos) + 1] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+      float h = 0.f, o = 0.f;
+      for (int gg = 0; gg < S; ++gg) df_add(h, o, red[2 * (gg * np + threadIdx.x)], red[2 * (gg * np + threadIdx.x) + 1]);
+      red[2 * LE_THREADS + 2 * threadIdx.x] = h;  // stage for the pairs of tr, dd
+      red[2 * LE_THREADS + 2 * threadIdx.x + 1] = o;
+      const double v = (double)h + (double)o;
+      if (idx < EP - 4) {
+        const int tile = idx >> 4, p = (idx >> 2) & 3, q = idx & 3;
+        if (tile < tm) {
+          const int i = 4 * (tile / kt) + p, j = 4 * (tile % kt) + q;
+          if (i < l && j < k) {
+            fin[i * k + j] = v;
+            st[i * k4 + j] = (float)(a.lam[i] * v);
+          }
         } else {
-          const int g2 = tile - tl.tm;
-          const int i = (g2 / tl.kt) * 4 + p, j = (g2 % tl.kt) * 4 + q;
-          if (i < k && j < k) rec[l * k + i * k + j] = (double)red[slot + e];
+          int bi, bj;
+          le_tri(tile - tm, kt, bi, bj);
+          const int i = 4 * bi + p, j = 4 * bj + q;
+          if (i < k && j < k) {
+            fin[lk + i * k + j] = v;
+            fin[lk + j * k + i] = v;
+            st[l * k4 + i * gp + j] = (float)v;
+            st[l * k4 + j * gp + i] = (float)v;
+            if (i == j) st[l * k4 + gp * gp + i] = 1.0f / ((float)v + a.alpha);
+            // (W^T W)_ij (H^T H)_ij over all (i, j): an off-diagonal tile holds each pair once
+            if (side == 1 && t >= 0) share += (bi == bj ? 1.0 : 2.0) * __ldcg(a.fin + lk + i * k + j) * v;
+          }
         }
       }
     }
     __syncthreads();
-  }
-  const double t2 = block_sum(tr, shd);
-  const double d2 = block_sum(dd, shd);
-  if (threadIdx.x == 0) {
-    rec[l * k + k * k] = t2;
-    rec[l * k + k * k + 1] = d2;
-  }
-}
-
-// Sliced reduction of all CTA records into fin: 16 lanes per entry, the
-// lanes' strided sums combined by a fixed xor tree (deterministic).
-__device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, double* fin) {
-  const int E = le_entries(a.l, a.k);
-  const int per = (E + gridDim.x - 1) / gridDim.x;
-  const int e0 = blockIdx.x * per, e1 = min(E, e0 + per);
-  const int grp = threadIdx.x >> 4, sub = threadIdx.x & 15;
-  for (int base = e0; base < e1; base += LE_THREADS / 16) {
-    const int e = base + grp;
-    double s = 0.0;
-    if (e < e1) {
-#pragma unroll 4
-      for (unsigned q = sub; q < gridDim.x; q += 16) s += __ldcg(a.part + (size_t)q * E + e);
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (e < e1 && sub == 0) fin[e] = s;
-  }
-}
-
-// M (lambda-scaled), G, 1 / (G_ii + alpha) from fin.
-__device__ __forceinline__ void le_load_state(const LaiArgs& a, const double* fin, float* Ms, float* Gs,
-                                              float* inv) {
-  const int k = a.k, l = a.l, k4 = (k + 3) & ~3;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < l * k4; e += LE_THREADS) {
-    const int i = e / k4, j = e - i * k4;
-    Ms[e] = j < k ? (float)(__ldg(a.lam + i) * __ldcg(fin + i * k + j)) : 0.f;
-  }
-#pragma unroll 4
-  for (int e = threadIdx.x; e < k * k4; e += LE_THREADS) {
-    const int i = e / k4, j = e - i * k4;
-    Gs[e] = j < k ? (float)__ldcg(fin + l * k + i * k + j) : 0.f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k4; i += LE_THREADS) inv[i] = i < k ? 1.0f / (Gs[i * k4 + i] + a.alpha) : 0.f;
-  __syncthreads();
-}
-
-// Objective after a full sweep (CTA 0): sum lambda^2 + sum GW .* GH - 2 tr + alpha dd.
-__device__ __forceinline__ void le_objective(const LaiArgs& a, int t, double* shd) {
-  const int k = a.k, l = a.l, E = le_entries(l, k);
-  const double* fw = a.fin;
-  const double* fh = a.fin + E;
-  double s2 = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += LE_THREADS) s2 += __ldcg(fw + l * k + e) * __ldcg(fh + l * k + e);
-  s2 = block_sum(s2, shd);
-  if (threadIdx.x == 0 && t < a.obj_cap)
-    a.obj[t] = a.normX2[0] + s2 - 2.0 * __ldcg(fh + l * k + k * k) + a.alpha_d * __ldcg(fh + l * k + k * k + 1);
-}
-
-// HALS update of one row (Eq. symhals_update2): y = U_r M with U_r read
-// through `u_at(p)`, the fixed row through `fx_at(i)`, the row being updated
-// through the reference `fu_ref(j)`.  Gives the row's F_upd . Y and
-// ||F_upd - F_fix||^2 in FP32 (the caller sums rows in FP64); returns true
-// when a non-finite value appeared.
-template <int KMAX, class UA, class FXA, class FUA>
-__device__ __forceinline__ bool le_row_update(float alpha, int l, int k, int k4q, const float4* Ms4,
-                                              const float4* Gs4, const float* inv, UA u_at, FXA fx_at, FUA fu_ref,
-                                              float& trow, float& drow) {
-  float y[KMAX], w[KMAX];
-#pragma unroll
-  for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
-  // Y_r = U_r M  (LAI product), float4 broadcast reads of M's rows
-  for (int p = 0; p < l; ++p) {
-    const float u = u_at(p);
-#pragma unroll
-    for (int c4 = 0; c4 < KMAX / 4; ++c4) {
-      if (c4 < k4q) {
-        const float4 m = Ms4[p * k4q + c4];
-        y[4 * c4 + 0] = fmaf(u, m.x, y[4 * c4 + 0]);
-        y[4 * c4 + 1] = fmaf(u, m.y, y[4 * c4 + 1]);
-        y[4 * c4 + 2] = fmaf(u, m.z, y[4 * c4 + 2]);
-        y[4 * c4 + 3] = fmaf(u, m.w, y[4 * c4 + 3]);
+    // tr and dd: hi/lo pairs at positions EP - 4 .. EP - 1
+    if (threadIdx.x < np && (idx == EP - 4 || idx == EP - 2)) {
+      float h = red[2 * LE_THREADS + 2 * threadIdx.x], o = red[2 * LE_THREADS + 2 * threadIdx.x + 1];
+      if (threadIdx.x + 1 < np) {
+        df_add(h, o, red[2 * LE_THREADS + 2 * threadIdx.x + 2], red[2 * LE_THREADS + 2 * threadIdx.x + 3]);
+        const double v = (double)h + (double)o;
+        const int e = lk + k * k + (idx == EP - 4 ? 0 : 1);
+        fin[e] = v;
+        if (side == 1 && t >= 0) share += (idx == EP - 4) ? -2.0 * v : a.alpha_d * v;  // -2 tr, + alpha dd
       }
     }
+    __syncthreads();
   }
+  if (side == 1 && t >= 0) {
+    share = block_sum(share, shd);
+    if (threadIdx.x == 0 && t < a.obj_cap)
+      a.objp[(size_t)t * gridDim.x + blockIdx.x] = share + (blockIdx.x == 0 ? a.normX2[0] : 0.0);
+  }
+}
+
+// The state written by le_reduce_slice for `side`, into shared memory [Ms | Gs | inv].
+__device__ __forceinline__ void le_load_state(const LaiArgs& a, int side, float* Ms) {
+  const int SL = le_state_floats(a.l, a.k, a.gp), SL4 = SL / 4;
+  const float4* src = reinterpret_cast<const float4*>(a.state + side * SL);
+  float4* dst = reinterpret_cast<float4*>(Ms);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < SL4; e += LE_THREADS) dst[e] = __ldcg(src + e);
+  __syncthreads();
+}
+
+// After the last sweep: obj[t] = sum of the CTAs' shares (CTA c takes sweeps c, c + grid, ...).
+__device__ __forceinline__ void le_objective_sums(const LaiArgs& a, double* shd) {
+  for (int t = blockIdx.x; t < a.nsweeps && t < a.obj_cap; t += gridDim.x) {
+    double s = 0.0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += LE_THREADS) s += __ldcg(a.objp + (size_t)t * gridDim.x + q);
+    s = block_sum(s, shd);
+    if (threadIdx.x == 0) a.obj[t] = s;
+  }
+}
+
+// Column updates of one row (Eq. symhals_update2) given its y = U_r M: the
+// fixed row read through `fx_at(i)`, the row being updated through the
+// reference `fu_ref(j)`.  G is KMAX x KMAX and 1 / (G_ii + alpha) KMAX long,
+// zero padded: columns i >= k come out 0 and the loop has no data-dependent
+// branches.  Four FMA chains per column.  Adds the row's F_upd . Y and
+// ||F_upd - F_fix||^2 to the double-float accumulators; returns true when a
+// non-finite value appeared.
+template <int KMAX, class FXA, class FUA>
+__device__ __forceinline__ bool le_hals_row(const float (&y)[KMAX], float alpha, int k, const float4* Gs4,
+                                            const float* inv, FXA fx_at, FUA fu_ref, float2& trv, float2& ddv) {
+  float w[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) w[j] = j < k ? fu_ref(j) : 0.f;
   // columns in order, each using the columns already updated (G symmetric: row i)
 #pragma unroll
   for (int i = 0; i < KMAX; ++i) {
-    if (i < k) {
-      float a0 = fmaf(alpha, fx_at(i), y[i]), a1 = 0.f;
+    const float hi = i < k ? fx_at(i) : 0.f;
+    float ac[4] = {fmaf(alpha, hi, y[i]), 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int j4 = 0; j4 < KMAX / 4; ++j4) {
-        if (j4 < k4q) {
-          const float4 g = Gs4[i * k4q + j4];
-          const float gv[4] = {g.x, g.y, g.z, g.w};
+    for (int j4 = 0; j4 < KMAX / 4; ++j4) {
+      const float4 g = Gs4[i * (KMAX / 4) + j4];
+      const float gv[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = 4 * j4 + q;
-            if (j != i) {  // pads of G are zero, so j >= k adds nothing
-              if (q & 1)
-                a1 = fmaf(-w[j], gv[q], a1);
-              else
-                a0 = fmaf(-w[j], gv[q], a0);
-            }
-          }
-        }
+      for (int q = 0; q < 4; ++q) {
+        const int j = 4 * j4 + q;
+        if (j != i) ac[q] = fmaf(-w[j], gv[q], ac[q]);
       }
-      w[i] = fmaxf((a0 + a1) * inv[i], 0.f);
     }
+    w[i] = fmaxf(((ac[0] + ac[1]) + (ac[2] + ac[3])) * inv[i], 0.f);
   }
   bool bad = false;
   float t0 = 0.f, t1 = 0.f, d0 = 0.f, d1 = 0.f;
@@ -263,78 +405,88 @@ __device__ __forceinline__ bool le_row_update(float alpha, int l, int k, int k4q
         d0 = fmaf(d, d, d0);
       }
     }
-  trow = t0 + t1;
-  drow = d0 + d1;
+  df_add_f(trv.x, trv.y, t0 + t1);
+  df_add_f(ddv.x, ddv.y, d0 + d1);
   return bad;
 }
 
 // ------------------------------------------------------------ resident rows
 
+// Column pitch: a multiple of 8 with 32 floats to spare, so that a column
+// shifted by its skew (up to 28 floats) never reaches the next one.
+__host__ __device__ inline int le_pitch(int rp) { return ((rp + 7) & ~7) + 32; }
+__host__ __device__ inline size_t le_resident_floats(int l, int k, int rp) {
+  const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3;
+  return (size_t)le_state_floats(l, k, le_gp(k)) + (size_t)(l4 + 3 * k4) * le_pitch(rp) + (size_t)16 * LE_THREADS;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const int k = a.k, l = a.l, RP = a.tile_rows;
+  const int k = a.k, l = a.l, RP = a.tile_rows, rq = RP / 4, P = a.pitch;
   const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3, k4q = k4 / 4;
   const int E = le_entries(l, k);
-  float* Ms = sm;             // l x k4, lambda-scaled, zero padded (float4 rows)
-  float* Gs = Ms + l * k4;    // k x k4, zero padded (symmetric: row i = column i)
-  float* inv = Gs + k * k4;   // k4
-  float* Ut = inv + k4;       // l4 x RP: column c of the CTA's U rows at Ut + c * RP
-  float* Wt = Ut + l4 * RP;   // k4 x RP
-  float* Ht = Wt + k4 * RP;   // k4 x RP
-  float* red = Ht + k4 * RP;  // LE_THREADS x 16: row-group combine
+  float* Ms = sm;               // l x k4, lambda-scaled, zero padded (float4 rows)
+  float* Gs = Ms + l * k4;      // KMAX x KMAX, zero padded (symmetric: row i = column i)
+  float* inv = Gs + KMAX * KMAX;  // KMAX
+  float* Ut = inv + KMAX;      // l4 columns: the CTA's rows of U
+  float* Wt = Ut + l4 * P;     // k4 columns
+  float* Ht = Wt + k4 * P;     // k4 columns
+  float* Yt = Ht + k4 * P;     // k4 columns: Y = U M of the current half
+  float* red = Yt + k4 * P;    // 16 x LE_THREADS
+  auto col = [P](int c) { return c * P + ((c >> 2) & 7) * 4; };  // start of column c
   __shared__ double shd[32];
 
   const int tid = threadIdx.x;
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
   const int R = (int)((a.n * (blockIdx.x + 1)) / gridDim.x - r0);
   const LeTiles tl = le_tiles(l4, k4);
-  float acc[4][16];
+  float acc[3][16];
 
   // prologue: the CTA's rows, transposed into shared memory (pads stay zero)
-  for (int e = tid; e < (l4 + 2 * k4) * RP; e += LE_THREADS) Ut[e] = 0.f;
+  for (int e = tid; e < (l4 + 3 * k4) * P; e += LE_THREADS) Ut[e] = 0.f;
   __syncthreads();
   {
     const float* Ug = a.U + r0 * l;
     for (int e = tid; e < R * l; e += LE_THREADS) {
       const int r = e / l, c = e - r * l;
-      Ut[c * RP + r] = __ldg(Ug + e);
+      Ut[col(c) + r] = __ldg(Ug + e);
     }
     const float* Wg = a.W + r0 * k;
     const float* Hg = a.H + r0 * k;
     for (int e = tid; e < R * k; e += LE_THREADS) {
       const int r = e / k, c = e - r * k;
-      Wt[c * RP + r] = Wg[e];
-      Ht[c * RP + r] = Hg[e];
+      Wt[col(c) + r] = Wg[e];
+      Ht[col(c) + r] = Hg[e];
     }
   }
   __syncthreads();
 
   // U^T F and F^T F over the CTA's rows, four rows per float4 step
   auto accumulate = [&](const float* Fu) {
-    const int rq = RP / 4;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < 3; ++t) {
       if (t >= tl.TPT) break;
       const int tile = le_tile_of(tl, t);
       if (tile < tl.T && tl.my_rg < tl.RG) {
-        const float* A;
-        int bj;
-        if (tile < tl.tm) {
-          A = Ut + (tile / tl.kt) * 4 * RP;
-          bj = (tile % tl.kt) * 4;
-        } else {
-          const int g = tile - tl.tm;
-          A = Fu + (g / tl.kt) * 4 * RP;
-          bj = (g % tl.kt) * 4;
+        int ab, bb;
+        bool au;
+        le_tile_rows(tl, tile, ab, bb, au);
+        const float* A = au ? Ut : Fu;
+        const float4* Ap[4];
+        const float4* Bp[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          Ap[p] = reinterpret_cast<const float4*>(A + col(4 * ab + p));
+          Bp[p] = reinterpret_cast<const float4*>(Fu + col(4 * bb + p));
         }
-        const float* B = Fu + bj * RP;
+#pragma unroll 2
         for (int c = tl.my_rg; c < rq; c += tl.RG) {
           float4 av[4], bv[4];
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
-            av[p] = reinterpret_cast<const float4*>(A + p * RP)[c];
-            bv[p] = reinterpret_cast<const float4*>(B + p * RP)[c];
+            av[p] = Ap[p][c];
+            bv[p] = Bp[p][c];
           }
 #pragma unroll
           for (int p = 0; p < 4; ++p)
@@ -355,39 +507,64 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
   // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
   le_clear(acc);
   accumulate(Ht);
-  le_finish(a, tl, acc, red, shd, 0.0, 0.0);
-  if (!grid_sync_bounded(a.bar, a.err)) return;
-  le_reduce_slice(a, a.fin + E);
-  if (!grid_sync_bounded(a.bar, a.err)) return;
-  le_load_state(a, a.fin + E, Ms, Gs, inv);
+  le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+  unsigned epoch = 0;
+  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  le_reduce_slice(a, 1, -1, red, shd);
+  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  le_load_state(a, 1, Ms);
 
   const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
   const float4* Gs4 = reinterpret_cast<const float4*>(Gs);
+
   for (int t = 0; t < a.nsweeps; ++t) {
     for (int side = 0; side < 2; ++side) {
       float* Fu = side ? Ht : Wt;
       const float* Fx = side ? Wt : Ht;
-      double tr = 0.0, dd = 0.0;
+      // Y = U M for the CTA's rows: 4 rows x 4 columns per thread (float4 of U
+      // down a column, broadcast float4 of a row of M)
+      for (int q = tid; q < rq * k4q; q += LE_THREADS) {
+        const int rb = q % rq, cb = q / rq;
+        float y[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) y[e] = 0.f;
+#pragma unroll 2
+        for (int p = 0; p < l; ++p) {
+          const float4 u = reinterpret_cast<const float4*>(Ut + col(p))[rb];
+          const float4 m = Ms4[p * k4q + cb];
+          const float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            y[i * 4 + 0] = fmaf(uv[i], m.x, y[i * 4 + 0]);
+            y[i * 4 + 1] = fmaf(uv[i], m.y, y[i * 4 + 1]);
+            y[i * 4 + 2] = fmaf(uv[i], m.z, y[i * 4 + 2]);
+            y[i * 4 + 3] = fmaf(uv[i], m.w, y[i * 4 + 3]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          reinterpret_cast<float4*>(Yt + col(4 * cb + j))[rb] = make_float4(y[j], y[4 + j], y[8 + j], y[12 + j]);
+      }
+      __syncthreads();
+      float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
       bool bad = false;
       for (int r = tid; r < R; r += LE_THREADS) {
-        float trow, drow;
-        bad |= le_row_update<KMAX>(
-            a.alpha, l, k, k4q, Ms4, Gs4, inv, [&](int p) { return Ut[p * RP + r]; },
-            [&](int i) { return Fx[i * RP + r]; }, [&](int j) -> float& { return Fu[j * RP + r]; }, trow, drow);
-        tr += (double)trow;
-        dd += (double)drow;
+        float y[KMAX];
+#pragma unroll
+        for (int c = 0; c < KMAX; ++c) y[c] = c < k ? Yt[col(c) + r] : 0.f;
+        bad |= le_hals_row<KMAX>(
+            y, a.alpha, k, Gs4, inv, [&](int i) { return Fx[col(i) + r]; },
+            [&](int j) -> float& { return Fu[col(j) + r]; }, trv, ddv);
       }
       if (bad) set_error(a.err, ERR_NAN);
       __syncthreads();
       le_clear(acc);
       accumulate(Fu);
-      le_finish(a, tl, acc, red, shd, tr, dd);
-      if (!grid_sync_bounded(a.bar, a.err)) return;
-      double* fin = a.fin + (side == 0 ? 0 : E);
-      le_reduce_slice(a, fin);
-      if (!grid_sync_bounded(a.bar, a.err)) return;
-      le_load_state(a, fin, Ms, Gs, inv);
-      if (side == 1 && blockIdx.x == 0) le_objective(a, t, shd);
+      le_finish(a, tl, acc, red, trv, ddv);
+      if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+      le_reduce_slice(a, side, t, red, shd);
+      if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+      le_load_state(a, side, Ms);
     }
   }
   // epilogue: the CTA's rows of W and H back to global memory
@@ -396,8 +573,8 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
     float* Hg = a.H + r0 * k;
     for (int e = tid; e < R * k; e += LE_THREADS) {
       const int r = e / k, c = e - r * k;
-      Wg[e] = Wt[c * RP + r];
-      Hg[e] = Ht[c * RP + r];
+      Wg[e] = Wt[col(c) + r];
+      Hg[e] = Ht[col(c) + r];
     }
   }
   // Grams after the last sweep for the handle's state: [0] = H^T H, [1] = W^T W
@@ -406,6 +583,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
       a.Gout[e] = __ldcg(a.fin + E + l * k + e);
       a.Gout[k * k + e] = __ldcg(a.fin + l * k + e);
     }
+  le_objective_sums(a, shd);
 }
 
 // ------------------------------------------------------------- streamed rows
@@ -418,19 +596,19 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
   const int E = le_entries(l, k);
   const int us = l4 + 1, fs = k4 + 1;   // odd row pitches: conflict-free per-row reads
   float* Ms = sm;                        // l x k4, lambda-scaled, zero padded (float4 rows)
-  float* Gs = Ms + l * k4;               // k x k4, zero padded (symmetric: row i = column i)
-  float* inv = Gs + k * k4;              // k4
-  float* Us = inv + k4;                  // TR x us: U rows of the tile
+  float* Gs = Ms + l * k4;               // KMAX x KMAX, zero padded (symmetric: row i = column i)
+  float* inv = Gs + KMAX * KMAX;         // KMAX
+  float* Us = inv + KMAX;                // TR x us: U rows of the tile
   float* Fx = Us + TR * us;              // TR x fs: fixed factor rows
   float* Fu = Fx + TR * fs;              // TR x fs: rows being updated
-  float* red = Fu + TR * fs;             // LE_THREADS x 16: row-group combine
+  float* red = Fu + TR * fs;             // 16 x LE_THREADS: row-group combine
   __shared__ double shd[32];
 
   const int tid = threadIdx.x;
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
   const int64_t r1 = (a.n * (blockIdx.x + 1)) / gridDim.x;
   const LeTiles tl = le_tiles(l4, k4);
-  float acc[4][16];
+  float acc[3][16];
 
   // pad columns (c >= l of U, c >= k of the factors) are zero once and for all;
   // rows past a tile's end are never read
@@ -457,24 +635,15 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
   // accumulate this tile's rows of U^T Fu and Fu^T Fu into acc (FP32)
   auto accumulate = [&](int rows) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < 3; ++t) {
       if (t >= tl.TPT) break;
       const int tile = le_tile_of(tl, t);
       if (tile < tl.T && tl.my_rg < tl.RG) {
-        const float* A;
-        int ai, sa, bj;
-        if (tile < tl.tm) {
-          ai = (tile / tl.kt) * 4;
-          bj = (tile % tl.kt) * 4;
-          A = Us;
-          sa = us;
-        } else {
-          const int g = tile - tl.tm;
-          ai = (g / tl.kt) * 4;
-          bj = (g % tl.kt) * 4;
-          A = Fu;
-          sa = fs;
-        }
+        int ab, bb;
+        bool au;
+        le_tile_rows(tl, tile, ab, bb, au);
+        const float* A = au ? Us : Fu;
+        const int sa = au ? us : fs, ai = 4 * ab, bj = 4 * bb;
         for (int rr = tl.my_rg; rr < rows; rr += tl.RG) {
           float av[4], bv[4];
 #pragma unroll
@@ -500,11 +669,12 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
     accumulate(rows);
     __syncthreads();
   }
-  le_finish(a, tl, acc, red, shd, 0.0, 0.0);
-  if (!grid_sync_bounded(a.bar, a.err)) return;
-  le_reduce_slice(a, a.fin + E);
-  if (!grid_sync_bounded(a.bar, a.err)) return;
-  le_load_state(a, a.fin + E, Ms, Gs, inv);
+  le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+  unsigned epoch = 0;
+  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  le_reduce_slice(a, 1, -1, red, shd);
+  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  le_load_state(a, 1, Ms);
 
   const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
   const float4* Gs4 = reinterpret_cast<const float4*>(Gs);
@@ -512,7 +682,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
     for (int side = 0; side < 2; ++side) {
       float* Fupd = side ? a.H : a.W;
       const float* Ffix = side ? a.W : a.H;
-      double tr = 0.0, dd = 0.0;
+      float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
       bool bad = false;
       le_clear(acc);
       for (int64_t b = r0; b < r1; b += TR) {
@@ -523,12 +693,26 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
           const float* ur = Us + tid * us;
           const float* hr = Fx + tid * fs;
           float* wr = Fu + tid * fs;
-          float trow, drow;
-          bad |= le_row_update<KMAX>(
-              a.alpha, l, k, k4q, Ms4, Gs4, inv, [&](int p) { return ur[p]; }, [&](int i) { return hr[i]; },
-              [&](int j) -> float& { return wr[j]; }, trow, drow);
-          tr += (double)trow;
-          dd += (double)drow;
+          // Y_r = U_r M, float4 broadcast reads of M's rows
+          float y[KMAX];
+#pragma unroll
+          for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
+          for (int p = 0; p < l; ++p) {
+            const float u = ur[p];
+#pragma unroll
+            for (int c4 = 0; c4 < KMAX / 4; ++c4) {
+              if (c4 < k4q) {
+                const float4 m = Ms4[p * k4q + c4];
+                y[4 * c4 + 0] = fmaf(u, m.x, y[4 * c4 + 0]);
+                y[4 * c4 + 1] = fmaf(u, m.y, y[4 * c4 + 1]);
+                y[4 * c4 + 2] = fmaf(u, m.z, y[4 * c4 + 2]);
+                y[4 * c4 + 3] = fmaf(u, m.w, y[4 * c4 + 3]);
+              }
+            }
+          }
+          bad |= le_hals_row<KMAX>(
+              y, a.alpha, k, Gs4, inv, [&](int i) { return hr[i]; }, [&](int j) -> float& { return wr[j]; }, trv,
+              ddv);
         }
         __syncthreads();
 #pragma unroll 4
@@ -540,13 +724,11 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
         __syncthreads();
       }
       if (bad) set_error(a.err, ERR_NAN);
-      le_finish(a, tl, acc, red, shd, tr, dd);
-      if (!grid_sync_bounded(a.bar, a.err)) return;
-      double* fin = a.fin + (side == 0 ? 0 : E);
-      le_reduce_slice(a, fin);
-      if (!grid_sync_bounded(a.bar, a.err)) return;
-      le_load_state(a, fin, Ms, Gs, inv);
-      if (side == 1 && blockIdx.x == 0) le_objective(a, t, shd);
+      le_finish(a, tl, acc, red, trv, ddv);
+      if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+      le_reduce_slice(a, side, t, red, shd);
+      if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+      le_load_state(a, side, Ms);
     }
   }
   // Grams after the last sweep for the handle's state: [0] = H^T H, [1] = W^T W
@@ -555,19 +737,24 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
       a.Gout[e] = __ldcg(a.fin + E + l * k + e);
       a.Gout[k * k + e] = __ldcg(a.fin + l * k + e);
     }
+  le_objective_sums(a, shd);
 }
 
-size_t lai_engine_part_doubles(int l, int k) { return (size_t)num_sms() * le_entries(l, k); }
-size_t lai_engine_fin_doubles(int l, int k) { return (size_t)2 * le_entries(l, k); }
+// Workspace layout (each piece 256-byte aligned): barrier counter, fin, objective
+// shares, records, state.
+static size_t le_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t lai_engine_ws_bytes(int l, int k, int obj_cap) {
+  const size_t grid = (size_t)num_sms();
+  return le_align(256) + le_align((size_t)2 * le_entries(l, k) * 8) + le_align((size_t)obj_cap * grid * 8) +
+         le_align(grid * le_row_groups(l, k) * le_rec_entries(l, k) * 4) +
+         le_align((size_t)2 * le_state_floats(l, k, le_gp(k)) * 4);
+}
 
 static size_t streamed_smem(int l, int k, int tr) {
   const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3;
-  return (size_t)(l * k4 + k * k4 + k4 + tr * (l4 + 1) + 2 * tr * (k4 + 1) + LE_THREADS * 16) * sizeof(float);
-}
-
-static size_t resident_smem(int l, int k, int rp) {
-  const int l4 = (l + 3) & ~3, k4 = (k + 3) & ~3;
-  return (size_t)((l + k + 1) * k4 + (l4 + 2 * k4) * rp + LE_THREADS * 16) * sizeof(float);
+  return ((size_t)le_state_floats(l, k, le_gp(k)) + (size_t)tr * (l4 + 1) + (size_t)2 * tr * (k4 + 1) +
+          (size_t)LE_THREADS * 16) * sizeof(float);
 }
 
 static size_t smem_optin_limit() {
@@ -585,10 +772,11 @@ static cudaError_t launch_engine(LaiArgs a, bool allow_resident, cudaStream_t st
   const int64_t rp = (rmax + 3) & ~3LL;
   const void* fn;
   size_t smem;
-  if (allow_resident && rp <= (1 << 20) && resident_smem(a.l, a.k, (int)rp) <= smem_optin_limit()) {
+  if (allow_resident && rp <= (1 << 20) && le_resident_floats(a.l, a.k, (int)rp) * 4 <= smem_optin_limit()) {
     fn = (const void*)lai_resident_kernel<KMAX>;
     a.tile_rows = (int)rp;
-    smem = resident_smem(a.l, a.k, (int)rp);
+    a.pitch = le_pitch((int)rp);
+    smem = le_resident_floats(a.l, a.k, (int)rp) * 4;
   } else {
     fn = (const void*)lai_streamed_kernel<KMAX>;
     // one tile per CTA when it fits (n = 2e4 gives ~132 rows per CTA)
@@ -608,12 +796,27 @@ static cudaError_t launch_engine(LaiArgs a, bool allow_resident, cudaStream_t st
 }
 
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
-                       int nsweeps, double alpha, const double* normX2, double* part, double* fin, double* obj,
-                       int obj_cap, double* Gout, unsigned* bar, unsigned* err, bool allow_resident,
-                       cudaStream_t st) {
-  if (k < 1 || k > 64 || l < 1 || l > 96 || n < 1) return cudaErrorInvalidValue;
-  LaiArgs a{U, lam, W, H, n, k, l, nsweeps, (float)alpha, alpha, normX2, part, fin, obj, obj_cap, Gout, bar, err, 256};
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * GRID_GEN * sizeof(unsigned), st);
+                       int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
+                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st) {
+  if (k < 1 || k > 64 || l < 1 || l > 96 || n < 1 || nsweeps > obj_cap) return cudaErrorInvalidValue;
+  char* b = static_cast<char*>(ws);
+  const size_t grid = (size_t)num_sms();
+  unsigned* bar = reinterpret_cast<unsigned*>(b);
+  b += le_align(256);
+  double* fin = reinterpret_cast<double*>(b);
+  b += le_align((size_t)2 * le_entries(l, k) * 8);
+  double* objp = reinterpret_cast<double*>(b);
+  b += le_align((size_t)obj_cap * grid * 8);
+  float* part = reinterpret_cast<float*>(b);
+  b += le_align(grid * le_row_groups(l, k) * le_rec_entries(l, k) * 4);
+  float* state = reinterpret_cast<float*>(b);
+  const int gp = le_gp(k);
+  LaiArgs a{U,    lam,   W,    H,   n,       k,    l,   nsweeps, (float)alpha, alpha, normX2, part,
+            fin,  state, objp, obj, obj_cap, Gout, bar, err,     256,          gp,    0};
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  // the state's pad entries are never written by the kernel
+  e = cudaMemsetAsync(state, 0, (size_t)2 * le_state_floats(l, k, gp) * sizeof(float), st);
   if (e != cudaSuccess) return e;
   if (k <= 8) return launch_engine<8>(a, allow_resident, st);
   if (k <= 16) return launch_engine<16>(a, allow_resident, st);

@@ -11,42 +11,42 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-// The arrival counter (bar[0]) and the generation word (bar[GRID_GEN]) sit in
-// different 128-byte lines, so that the spinning readers of the generation do
-// not contend with the arrivals.  bar must hold 2 * GRID_GEN words, zeroed
-// before the launch.  Waits are bounded (1 s of %globaltimer): on expiry the
-// waiting CTA sets ERR_TIMEOUT and every CTA leaves at its next barrier.
-// Returns false (on every thread of the block) when the barrier gave up.
-constexpr int GRID_GEN = 32;
-
-__device__ inline bool grid_sync_bounded(unsigned* bar, unsigned* err) {
+// Grid barrier on a monotonic arrival counter bar[0] (zeroed before the
+// launch).  Barrier number e (1, 2, ...) of the launch completes when the
+// counter reaches e * gridDim.x: every CTA adds 1 (a fire-and-forget
+// reduction after a fence that publishes its writes) and thread 0 polls the
+// counter with acquire loads.  `epoch` counts the barriers passed (thread 0's
+// copy is the one used).  Waits are bounded (1 s of %globaltimer): on expiry
+// the waiting CTA sets ERR_TIMEOUT, and every CTA that sees that bit leaves
+// at its next barrier.  Returns false (on every thread of the block) when the
+// barrier gave up.
+__device__ inline bool grid_sync_bounded(unsigned* bar, unsigned* err, unsigned& epoch) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + GRID_GEN;
-    const unsigned g = *gen;
+    epoch += 1u;
+    const unsigned target = epoch * gridDim.x;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    atomicAdd(bar, 1u);
     ok = 1;
-    if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + GRID_GEN, 1u);
-    } else {
-      const uint64_t t0 = global_timer_ns();
-      unsigned spins = 0;
-      while (*gen == g) {
-        __nanosleep(32);
-        if ((++spins & 63u) == 0) {
-          if (*(volatile unsigned*)err & ERR_TIMEOUT) {
-            ok = 0;
-            break;
-          }
-          if (global_timer_ns() - t0 > 1000000000ull) {
-            atomicOr(err, ERR_TIMEOUT);
-            ok = 0;
-            break;
-          }
+    uint64_t t0 = 0;
+    for (unsigned spins = 1;; ++spins) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if (spins > 32u) __nanosleep(32);
+      if ((spins & 63u) == 0) {
+        if (*(volatile unsigned*)err & ERR_TIMEOUT) {
+          ok = 0;
+          break;
+        }
+        const uint64_t now = global_timer_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > 1000000000ull) {
+          atomicOr(err, ERR_TIMEOUT);
+          ok = 0;
+          break;
         }
       }
     }
