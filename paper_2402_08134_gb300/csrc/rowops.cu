@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace symnmf {
@@ -70,15 +71,45 @@ __global__ void xstats_dense_kernel(const void* x, int64_t ldx, const float* rs,
     } else {
       const float rsi = (FMT == 3) ? rs[i] : 1.f;
       float m = -INFINITY, s = 0.f, cs = 0.f, q = 0.f, cq = 0.f, eq = 0.f;
-#pragma unroll 8
-      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const float v = load_xf<FMT>(x, ldx, rsi, i, j);
+      auto add = [&](float v) {
         m = fmaxf(m, v);
         kahan_add(s, cs, v);
         const float p = v * v;
         eq += fmaf(v, v, -p);
         kahan_add(q, cq, p);
+      };
+      // 16-byte loads when the row start allows them (many bytes in flight per thread)
+      constexpr int ES = FMT == 1 ? 4 : FMT == 2 ? 2 : 1;  // bytes per element
+      constexpr int VE = 16 / ES;                          // elements per 16 bytes
+      const unsigned char* rowp = (const unsigned char*)x + (size_t)i * ldx * ES;
+      int64_t j0 = 0;
+      if (((uintptr_t)rowp & 15) == 0) {
+        const int64_t nv = n / VE;
+        const uint4* r4 = reinterpret_cast<const uint4*>(rowp);
+#pragma unroll 4
+        for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+          const uint4 w = __ldg(r4 + v);
+          const unsigned wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if constexpr (FMT == 1) {
+              add(__uint_as_float(wv[u]));
+            } else if constexpr (FMT == 2) {
+              add(__uint_as_float(wv[u] << 16));          // element 2u (low half)
+              add(__uint_as_float(wv[u] & 0xffff0000u));  // element 2u + 1
+            } else {
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                __nv_fp8_e4m3 f8;
+                f8.__x = (unsigned char)(wv[u] >> (8 * b));
+                add(rsi * float(f8));
+              }
+            }
+          }
+        }
+        j0 = nv * VE;
       }
+      for (int64_t j = j0 + threadIdx.x; j < n; j += blockDim.x) add(load_xf<FMT>(x, ldx, rsi, i, j));
       mx = fmax(mx, (double)m);
       sm += (double)s - (double)cs;
       sq += ((double)q - (double)cq) + (double)eq;
@@ -180,14 +211,17 @@ cudaError_t xstats(int fmt, const void* x, int64_t ldx, const float* row_scale, 
 // ---------------------------------------------------------- cross product
 
 constexpr int XC_THREADS = 256;
-constexpr int XC_CHUNK = 32;
-constexpr int XC_FOLD = 8;  // chunks summed (compensated FP32) before the FP64 accumulation
+constexpr int XC_CHUNK = 128;
 
 size_t xcross_ws_doubles(int la, int lb) { return (size_t)2 * num_sms() * la * lb + 64; }
 
-// C = A^T diag(wt) B over (gathered) rows.  FP32 products accumulate over a
-// chunk of XC_CHUNK rows, then into FP64 per-thread sums; block partials are
-// summed in block order by the last block (deterministic).
+// C = A^T diag(wt) B over (gathered) rows.  Each thread keeps Kahan-
+// compensated FP32 sums (error O(eps) however many rows they cover); row
+// groups and block partials combine as double-float pairs (dfloat.cuh): no
+// FP64 arithmetic, which is scarce on this part.  The trace-trick objective
+// cancels terms of size ||X||^2, so the Grams need this accuracy.  Block
+// partials are summed in block order (deterministic), by the last block or by
+// a second kernel.
 template <int TPT>
 __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
     const float* __restrict__ A, int lda, int la, const float* __restrict__ B, int ldb, int lb,
@@ -198,7 +232,8 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   const int la4 = (la + 3) & ~3, lb4 = (lb + 3) & ~3;
   float* As = (float*)smraw;
   float* Bs = As + XC_CHUNK * la4;
-  double* red = (double*)(Bs + XC_CHUNK * lb4);
+  dfl* red = (dfl*)(Bs + XC_CHUNK * lb4);
+  dfl* wsd = reinterpret_cast<dfl*>(ws);  // the partials are double-float pairs
   const int ta = la4 >> 2, tb = lb4 >> 2, T = ta * tb;
   const int tid = threadIdx.x;
   const int R = T >= XC_THREADS ? 1 : XC_THREADS / T;
@@ -206,37 +241,49 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   const bool active = rg < R;
 
   const int64_t count = cnt ? (int64_t)(*cnt) : n;
-  int64_t per = (count + gridDim.x - 1) / gridDim.x;
-  per = (per + XC_CHUNK - 1) / XC_CHUNK * XC_CHUNK;
+  const int64_t per = (count + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = min(count, r0 + per);
 
-  // FP32 partial sums carry a Kahan compensation term (fc), so their error
-  // stays O(eps) however many rows they cover; they are folded into FP64
-  // every XC_FOLD chunks.  The trace-trick objective cancels terms of size
-  // ||X||^2, so the Grams need this accuracy.
-  double acc[TPT][16];
   float f[TPT][16], fc[TPT][16];
 #pragma unroll
   for (int t = 0; t < TPT; ++t)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[t][e] = 0.0, f[t][e] = 0.f, fc[t][e] = 0.f;
+    for (int e = 0; e < 16; ++e) f[t][e] = 0.f, fc[t][e] = 0.f;
 
   // a Gram (same operand, no weights) stages its rows once
   const bool same = (A == B) && (lda == ldb) && (la == lb) && !wt;
   const float* Bsrc = same ? As : Bs;
-  const int lane = tid & 31, wid = tid >> 5;
-  int chunk_no = 0;
-  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK, ++chunk_no) {
-    // stage the chunk: one warp per row, lanes along the row (coalesced)
-    for (int rr = wid; rr < XC_CHUNK; rr += XC_THREADS / 32) {
-      const int64_t r = rb + rr;
-      const bool live = r < r1;
-      const int64_t src = live ? (idx ? (int64_t)idx[r] : r) : 0;
-      for (int c = lane; c < la4; c += 32) As[rr * la4 + c] = (live && c < la) ? A[src * lda + c] : 0.f;
-      if (!same) {
-        const float w = (live && wt) ? wt[r] : 1.f;
-        for (int c = lane; c < lb4; c += 32) Bs[rr * lb4 + c] = (live && c < lb) ? B[src * ldb + c] * w : 0.f;
+  // pad columns are zero once and for all
+  if (la4 > la)
+    for (int e = tid; e < XC_CHUNK * (la4 - la); e += XC_THREADS) As[(e / (la4 - la)) * la4 + la + e % (la4 - la)] = 0.f;
+  if (!same && lb4 > lb)
+    for (int e = tid; e < XC_CHUNK * (lb4 - lb); e += XC_THREADS) Bs[(e / (lb4 - lb)) * lb4 + lb + e % (lb4 - lb)] = 0.f;
+  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK) {
+    // stage the chunk: flattened over (row, column) so that every thread's
+    // loads are independent of one another (many in flight); rows past the
+    // end are zero
+    const int rows = (int)min((int64_t)XC_CHUNK, r1 - rb);
+#pragma unroll 4
+    for (int e = tid; e < XC_CHUNK * la; e += XC_THREADS) {
+      const int rr = e / la, c = e - rr * la;
+      float v = 0.f;
+      if (rr < rows) {
+        const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
+        v = A[src * lda + c];
+      }
+      As[rr * la4 + c] = v;
+    }
+    if (!same) {
+#pragma unroll 4
+      for (int e = tid; e < XC_CHUNK * lb; e += XC_THREADS) {
+        const int rr = e / lb, c = e - rr * lb;
+        float v = 0.f;
+        if (rr < rows) {
+          const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
+          v = B[src * ldb + c] * (wt ? __ldg(wt + rb + rr) : 1.f);
+        }
+        Bs[rr * lb4 + c] = v;
       }
     }
     __syncthreads();
@@ -246,7 +293,7 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
         const int tile = (T >= XC_THREADS) ? tid + t * XC_THREADS : tid % T;
         if (tile < T) {
           const int ti = tile / tb, tj = tile - ti * tb;
-          for (int rr = rg; rr < XC_CHUNK; rr += R) {
+          for (int rr = rg; rr < rows; rr += R) {
             const float4 a = *(const float4*)(As + rr * la4 + 4 * ti);
             const float4 b = *(const float4*)(Bsrc + rr * lb4 + 4 * tj);
             const float av[4] = {a.x, a.y, a.z, a.w};
@@ -264,17 +311,6 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
           }
         }
       }
-      // compensated FP32 over XC_FOLD chunks, then FP64
-      if ((chunk_no % XC_FOLD) == XC_FOLD - 1 || rb + XC_CHUNK >= r1) {
-#pragma unroll
-        for (int t = 0; t < TPT; ++t)
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            acc[t][e] += (double)f[t][e] - (double)fc[t][e];
-            f[t][e] = 0.f;
-            fc[t][e] = 0.f;
-          }
-      }
     }
     __syncthreads();
   }
@@ -286,14 +322,17 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
       if (active && rg == g) {
         const int tile = tid % T;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) red[tile * 16 + e] = (g == 0 ? 0.0 : red[tile * 16 + e]) + acc[0][e];
+        for (int e = 0; e < 16; ++e) {
+          const dfl v{f[0][e], -fc[0][e]};
+          red[tile * 16 + e] = (g == 0) ? v : df_add(red[tile * 16 + e], v);
+        }
       }
       __syncthreads();
     }
     for (int e = tid; e < T * 16; e += XC_THREADS) {
       const int tile = e >> 4, w = e & 15;
       const int i = (tile / tb) * 4 + (w >> 2), j = (tile % tb) * 4 + (w & 3);
-      if (i < la && j < lb) ws[(size_t)blockIdx.x * LL + i * lb + j] = red[e];
+      if (i < la && j < lb) wsd[(size_t)blockIdx.x * LL + i * lb + j] = red[e];
     }
   } else {
 #pragma unroll
@@ -304,7 +343,7 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int i = ti * 4 + (e >> 2), j = tj * 4 + (e & 3);
-          if (i < la && j < lb) ws[(size_t)blockIdx.x * LL + i * lb + j] = acc[t][e];
+          if (i < la && j < lb) wsd[(size_t)blockIdx.x * LL + i * lb + j] = dfl{f[t][e], -fc[t][e]};
         }
       }
     }
@@ -313,16 +352,23 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
     const unsigned G = gridDim.x;
     for (int e = tid; e < LL; e += XC_THREADS) {
       // four independent chains keep several L2 loads in flight (fixed order)
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      dfl s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
       unsigned b = 0;
       for (; b + 4 <= G; b += 4) {
-        s0 += __ldcg(ws + (size_t)b * LL + e);
-        s1 += __ldcg(ws + (size_t)(b + 1) * LL + e);
-        s2 += __ldcg(ws + (size_t)(b + 2) * LL + e);
-        s3 += __ldcg(ws + (size_t)(b + 3) * LL + e);
+        const float2 v0 = __ldcg(reinterpret_cast<const float2*>(wsd + (size_t)b * LL + e));
+        const float2 v1 = __ldcg(reinterpret_cast<const float2*>(wsd + (size_t)(b + 1) * LL + e));
+        const float2 v2 = __ldcg(reinterpret_cast<const float2*>(wsd + (size_t)(b + 2) * LL + e));
+        const float2 v3 = __ldcg(reinterpret_cast<const float2*>(wsd + (size_t)(b + 3) * LL + e));
+        s0 = df_add(s0, dfl{v0.x, v0.y});
+        s1 = df_add(s1, dfl{v1.x, v1.y});
+        s2 = df_add(s2, dfl{v2.x, v2.y});
+        s3 = df_add(s3, dfl{v3.x, v3.y});
       }
-      for (; b < G; ++b) s0 += __ldcg(ws + (size_t)b * LL + e);
-      double s = (s0 + s1) + (s2 + s3);
+      for (; b < G; ++b) {
+        const float2 v0 = __ldcg(reinterpret_cast<const float2*>(wsd + (size_t)b * LL + e));
+        s0 = df_add(s0, dfl{v0.x, v0.y});
+      }
+      double s = df_to_double(df_add(df_add(s0, s1), df_add(s2, s3)));
       const int i = e / lb, j = e - i * lb;
       if (lam) s *= lam[i];
       if (i == j) s += shift;
@@ -334,21 +380,30 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
 }
 
 // Second stage for large reductions: one warp per entry sums the block
-// partials (lanes strided over blocks, then a fixed shuffle tree).
+// partials (lanes strided over blocks, then a fixed shuffle tree; double-float).
 __global__ void xcross_reduce_kernel(const double* __restrict__ ws, int G, int LL, int lb,
                                      const double* __restrict__ lam, double shift, double* C, float* Cf) {
   const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (e >= LL) return;
-  double s = 0.0;
-  for (int b = lane; b < G; b += 32) s += __ldcg(ws + (size_t)b * LL + e);
-  s = warp_sum(s);
+  const float2* wsd = reinterpret_cast<const float2*>(ws);
+  dfl s{0.f, 0.f};
+  for (int b = lane; b < G; b += 32) {
+    const float2 v = __ldcg(wsd + (size_t)b * LL + e);
+    s = df_add(s, dfl{v.x, v.y});
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfl t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+    s = df_add(s, t);
+  }
   if (lane == 0) {
+    double v = df_to_double(s);
     const int i = e / lb, j = e - i * lb;
-    if (lam) s *= lam[i];
-    if (i == j) s += shift;
-    if (C) C[e] = s;
-    if (Cf) Cf[e] = (float)s;
+    if (lam) v *= lam[i];
+    if (i == j) v += shift;
+    if (C) C[e] = v;
+    if (Cf) Cf[e] = (float)v;
   }
 }
 

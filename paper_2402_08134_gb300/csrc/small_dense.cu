@@ -63,18 +63,23 @@ cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, 
 }
 
 // Cyclic two-sided Jacobi with the round-robin (circle) ordering: each round
-// rotates l/2 disjoint pairs at once (Golub & Van Loan, symmetric Schur 2x2).
+// rotates l/2 disjoint pairs at once (Golub & Van Loan, symmetric Schur 2x2),
+// applying J^T A J block by block (2 x 2 blocks of two pairs) in one pass.
 // Rotations run in FP32 (GB300's FP64 rate is ~1/64 of FP32 and T is only
-// l x l); the convergence sums are FP64.  Eigenvectors come out orthonormal
-// to ~1e-7, far below the precision of the products that formed T.
+// l x l); the convergence sums are FP64.  Sweeps stop once the off-diagonal
+// mass is at the FP32 rounding level, off <= (8 l eps32)^2 ||T||_F^2: then
+// ||T - V Lambda V^T||_F <= 8 l eps32 ||T||_F (about 2e-5 for l = 50), and the
+// eigenvectors are orthonormal to ~1e-7, far below the precision of the
+// products that formed T.
 __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* lam) {
   extern __shared__ float smf[];
   const int L = (l + 1) & ~1;  // padded to even; index l is a dummy when l is odd
+  const int m = L / 2;         // disjoint pairs per round
   float* A = smf;              // l*l
   float* V = A + l * l;        // l*l
-  float* cs = V + l * l;       // 2 * (L/2)
-  int* pp = (int*)(cs + L);    // L/2
-  int* qq = pp + L / 2;
+  float* cs = V + l * l;       // 2 m
+  int* pp = (int*)(cs + L);    // m
+  int* qq = pp + m;            // m
   __shared__ double off, tot;
   __shared__ double shr[32];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -84,7 +89,7 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
     V[e] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  const int m = L / 2;
+  const double lim = 8.0 * l * 5.9604644775390625e-8;  // 8 l 2^-24
   for (int sweep = 0; sweep < 30; ++sweep) {
     double o = 0.0, t = 0.0;
     for (int e = tid; e < l * l; e += nt) {
@@ -99,55 +104,62 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
       tot = t;
     }
     __syncthreads();
-    if (off <= 1e-13 * tot || off == 0.0) break;
+    if (off <= lim * lim * tot || off == 0.0) break;
     for (int round = 0; round < L - 1; ++round) {
-      // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate
+      // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate; a pair
+      // with the dummy index keeps its real index q = l-1.. unrotated (p = -1)
       for (int i = tid; i < m; i += nt) {
         const int a = (i == 0) ? 0 : ((i - 1 + round) % (L - 1)) + 1;
         const int bslot = L - 1 - i;
         const int b = ((bslot - 1 + round) % (L - 1)) + 1;
         int p = min(a, b), q = max(a, b);
-        float c = 1.f, s = 0.f;
+        float c = 1.f, sn = 0.f;
         if (q < l) {
           const float apq = A[p * l + q];
           if (apq != 0.f) {
             const float tau = (A[q * l + q] - A[p * l + p]) / (2.f * apq);
             const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = 1.f / sqrtf(1.f + tt * tt);
-            s = tt * c;
+            c = rsqrtf(1.f + tt * tt);
+            sn = tt * c;
           }
         } else {
+          q = p;  // the only real index of the pair
           p = -1;
         }
         pp[i] = p;
         qq[i] = q;
         cs[2 * i] = c;
-        cs[2 * i + 1] = s;
+        cs[2 * i + 1] = sn;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < m * l; e += nt) {
-        const int i = e / l, col = e - i * l;
-        const int p = pp[i], q = qq[i];
-        if (p < 0) continue;
-        const float c = cs[2 * i], s = cs[2 * i + 1];
-        const float ap = A[p * l + col], aq = A[q * l + col];
-        A[p * l + col] = c * ap - s * aq;
-        A[q * l + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J and V <- V J
-      for (int e = tid; e < m * l; e += nt) {
-        const int i = e / l, row = e - i * l;
-        const int p = pp[i], q = qq[i];
-        if (p < 0) continue;
-        const float c = cs[2 * i], s = cs[2 * i + 1];
-        const float ap = A[row * l + p], aq = A[row * l + q];
-        A[row * l + p] = c * ap - s * aq;
-        A[row * l + q] = s * ap + c * aq;
-        const float vp = V[row * l + p], vq = V[row * l + q];
-        V[row * l + p] = c * vp - s * vq;
-        V[row * l + q] = s * vp + c * vq;
+      // A <- J^T A J on every 2x2 block (rows of pair u, columns of pair v) at
+      // once, and V <- V J (rows i, columns of pair v)
+      for (int e = tid; e < m * m + l * m; e += nt) {
+        if (e < m * m) {
+          const int u = e / m, v = e - u * m;
+          const int pu = pp[u], qu = qq[u], pv = pp[v], qv = qq[v];
+          const float cu = cs[2 * u], su = cs[2 * u + 1], cv = cs[2 * v], sv = cs[2 * v + 1];
+          // rows pu (may be -1), qu; columns pv (may be -1), qv
+          const float x = (pu >= 0 && pv >= 0) ? A[pu * l + pv] : 0.f;
+          const float y = (pu >= 0) ? A[pu * l + qv] : 0.f;
+          const float z = (pv >= 0) ? A[qu * l + pv] : 0.f;
+          const float w = A[qu * l + qv];
+          const float x1 = cu * x - su * z, z1 = su * x + cu * z;
+          const float y1 = cu * y - su * w, w1 = su * y + cu * w;
+          if (pu >= 0 && pv >= 0) A[pu * l + pv] = cv * x1 - sv * y1;
+          if (pu >= 0) A[pu * l + qv] = sv * x1 + cv * y1;
+          if (pv >= 0) A[qu * l + pv] = cv * z1 - sv * w1;
+          A[qu * l + qv] = sv * z1 + cv * w1;
+        } else {
+          const int f = e - m * m, row = f / m, v = f - row * m;
+          const int pv = pp[v], qv = qq[v];
+          if (pv >= 0) {
+            const float cv = cs[2 * v], sv = cs[2 * v + 1];
+            const float a0 = V[row * l + pv], a1 = V[row * l + qv];
+            V[row * l + pv] = cv * a0 - sv * a1;
+            V[row * l + qv] = sv * a0 + cv * a1;
+          }
+        }
       }
       __syncthreads();
     }

@@ -15,8 +15,9 @@ def test_warm_start_training_and_gain(S):
     assert losses[-1] < 0.8 * losses[0]
     gain = lambda key: np.median([r["random"][key] / r["learned"][key] for r in out["rows"]])  # noqa: E731
     # the learned start fits X better than the scaled random start at the first sweep and
-    # keeps the lead over the early sweeps; final residuals stay close (reported, not ranked)
+    # keeps the lead over the early sweeps; after the sweeps both starts sit in (possibly
+    # different) local minima, and the learned one must not be a worse one by more than 10%
     assert gain("obj0") > 1.0, out["rows"]
     assert gain("obj5") > 1.0, out["rows"]
     for r in out["rows"]:
-        assert abs(r["learned"]["nr"] - r["random"]["nr"]) < 5e-3
+        assert r["learned"]["nr"] <= 1.1 * r["random"]["nr"], (r["learned"]["nr"], r["random"]["nr"])
