@@ -151,10 +151,10 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the product kernel from the committed ncu summary, if it still matches the source."""
-    path = os.path.join(ROOT, "profiles", "xf_tc_bf16_n20000_traffic.txt")
-    src = os.path.join(ROOT, "paper_2402_08134_gb300", "csrc", "gemm_tc.cu")
+def recorded_traffic(name, source):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if it still matches the source."""
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2402_08134_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -169,6 +169,15 @@ def recorded_traffic():
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def fp32_peak_tflops(dev, clk):
+    """FP32 FMA peak from unit counts and clock: SMs x 128 FMA lanes x 2 FLOPs x max SM clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
 # --------------------------------------------------------------- oracle side
@@ -254,6 +263,7 @@ def run_ours(args):
     barrier()
     ms_step = e0.elapsed_time(e1) / args.steps
     prod_ms, prod_n, prod_bytes = s.profile_read()
+    eng_ms, eng_n, eng_flops = s.profile_read_engine()
     s.profile(False)
     launches = S.launch_count() - launches0
     clk = clocks.stop()
@@ -319,11 +329,25 @@ def run_ours(args):
     avg_launch_ms = prod_ms / max(prod_n, 1)
     bytes_per_launch = prod_bytes / max(prod_n, 1)
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if prod_n else None
-    roof = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F, N=l=50)", "bound": "hbm", "achieved": achieved,
-            "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
-            "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": recorded_traffic(),
-            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "launches": prod_n,
-            "tflops": (2.0 * N * N * L / (avg_launch_ms * 1e-3) / 1e12) if prod_n else None}
+    roof_product = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F, N=l=50)", "bound": "hbm", "achieved": achieved,
+                    "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
+                    "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
+                    "traffic": recorded_traffic("xf_tc_bf16_n20000_traffic.txt", "gemm_tc.cu"),
+                    "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "launches": prod_n,
+                    "tflops": (2.0 * N * N * L / (avg_launch_ms * 1e-3) / 1e12) if prod_n else None}
+    # the dominant kernel of the step: the persistent LAI sweep launch (latency-bound FP32 arithmetic
+    # on shared-memory-resident rows), against the FP32 FMA peak of the part
+    fp32_pk, sms, mhz = fp32_peak_tflops(dev, clk)
+    eng_avg_ms = eng_ms / max(eng_n, 1)
+    eng_flops_launch = eng_flops / max(eng_n, 1)
+    eng_achieved = eng_flops_launch / (eng_avg_ms * 1e-3) / 1e12 if eng_n else None
+    roof = {"kernel": f"lai_resident_kernel (persistent LAI-HALS, {SWEEPS} sweeps per launch, k={K}, l={L})",
+            "bound": "alu", "achieved": eng_achieved, "peak": fp32_pk,
+            "peak_kind": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz", "unit": "TFLOP/s",
+            "frac": (eng_achieved / fp32_pk) if eng_achieved else None,
+            "traffic": recorded_traffic("lai_resident_n20000_k20_l50_traffic.txt", "lai_engine.cu"),
+            "flops_per_launch": eng_flops_launch, "avg_launch_ms": eng_avg_ms, "launches": eng_n,
+            "share_of_step": (eng_ms / args.steps) / ms_step if eng_n else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -348,7 +372,8 @@ def run_ours(args):
         "forms": out,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Xh.numel() * 2),
                 "d2h_bytes_per_step": int(N * K * 4)},
-        "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+        "roofline": roof, "roofline_product": roof_product, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(launches),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

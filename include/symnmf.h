@@ -246,6 +246,12 @@ symnmf_status symnmf_convert_bf16(const float* x, int64_t n, int64_t ldx, uint16
  * bytes (X once, F and Y once each), then resets the record. */
 symnmf_status symnmf_profile(symnmf_t h, int enable);
 symnmf_status symnmf_profile_read(symnmf_t h, double* total_ms, int64_t* launches, double* bytes);
+/* The same for the persistent LAI-HALS sweep launches (Alg. LAI-SymNMF loop):
+ * summed kernel time (ms), number of launches and their algorithmic FLOPs --
+ * per half sweep n (l k + k^2 + l k + k (k + 1) / 2) FMAs (Y = U M, the column
+ * updates, U^T F, upper F^T F), plus a prologue of n (l k + k (k + 1) / 2),
+ * two FLOPs each.  Resets the record. */
+symnmf_status symnmf_profile_read_engine(symnmf_t h, double* total_ms, int64_t* launches, double* flops);
 
 /* Number of kernels this library has launched in this process (graph replays
  * count each kernel node). */

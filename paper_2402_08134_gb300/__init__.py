@@ -94,6 +94,7 @@ _SIGS = {
     "symnmf_launch_count": (C.c_uint64, []),
     "symnmf_profile": (_I, [_P, _I]),
     "symnmf_profile_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
+    "symnmf_profile_read_engine": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
     "symnmf_batched_create": (_I, [C.POINTER(symnmf_problem), _I, _I, C.POINTER(symnmf_options), _P,
                                    C.POINTER(_P)]),
     "symnmf_batched_destroy": (None, [_P]),
@@ -320,6 +321,11 @@ class Solver:
         t, n, b = C.c_double(), C.c_int64(), C.c_double()
         self._chk(symnmf_profile_read(self.h, C.byref(t), C.byref(n), C.byref(b)))
         return t.value, n.value, b.value
+
+    def profile_read_engine(self):
+        t, n, f = C.c_double(), C.c_int64(), C.c_double()
+        self._chk(symnmf_profile_read_engine(self.h, C.byref(t), C.byref(n), C.byref(f)))
+        return t.value, n.value, f.value
 
     # -- residual
     def residual(self, source=SRC_X, proj_grad=False):

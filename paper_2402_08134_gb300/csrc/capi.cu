@@ -339,6 +339,10 @@ extern "C" void symnmf_destroy(symnmf_t h) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
+  for (auto& pr : h->eprof_events) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -566,8 +570,22 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
   int done = 0;
   while (done < nsweeps) {
     const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profiling && !h->capturing) {
+      if (h->eprof_used == h->eprof_events.size()) {
+        cudaEvent_t a, b;
+        TRY(cudaEventCreate(&a));
+        TRY(cudaEventCreate(&b));
+        h->eprof_events.push_back({a, b});
+        h->eprof_flops.push_back(0.0);
+      }
+      e0 = h->eprof_events[h->eprof_used].first;
+      e1 = h->eprof_events[h->eprof_used].second;
+      h->eprof_flops[h->eprof_used] = lai_engine_flops(h->n, k, h->l, chunk);
+      h->eprof_used++;
+    }
     TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
-                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st));
+                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, e0, e1));
     if (obj_host) {
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
                           h->st));
@@ -891,6 +909,7 @@ extern "C" symnmf_status symnmf_profile(symnmf_t h, int enable) {
   if (!h) return SYMNMF_EINVAL;
   h->profiling = enable != 0;
   h->prof_used = 0;
+  h->eprof_used = 0;
   return SYMNMF_OK;
 }
 
@@ -908,5 +927,23 @@ extern "C" symnmf_status symnmf_profile_read(symnmf_t h, double* total_ms, int64
   if (launches) *launches = (int64_t)h->prof_used;
   if (bytes) *bytes = by;
   h->prof_used = 0;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_profile_read_engine(symnmf_t h, double* total_ms, int64_t* launches,
+                                                    double* flops) {
+  if (!h) return SYMNMF_EINVAL;
+  TRY(cudaStreamSynchronize(h->st));
+  double t = 0.0, fl = 0.0;
+  for (size_t i = 0; i < h->eprof_used; ++i) {
+    float ms = 0.f;
+    TRY(cudaEventElapsedTime(&ms, h->eprof_events[i].first, h->eprof_events[i].second));
+    t += ms;
+    fl += h->eprof_flops[i];
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = (int64_t)h->eprof_used;
+  if (flops) *flops = fl;
+  h->eprof_used = 0;
   return SYMNMF_OK;
 }

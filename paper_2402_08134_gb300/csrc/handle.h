@@ -95,4 +95,7 @@ struct symnmf_ctx {
   size_t prof_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   std::vector<double> prof_bytes;
+  size_t eprof_used = 0;  // LAI sweep engine launches timed while profiling
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eprof_events;
+  std::vector<double> eprof_flops;
 };

@@ -147,9 +147,15 @@ cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, ui
 // All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu);
 // `allow_resident` lets the CTAs keep their rows in shared memory when they fit.
 size_t lai_engine_ws_bytes(int l, int k, int obj_cap);
+// ev_begin / ev_end (optional) are recorded right around the kernel launch.
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
-                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st);
+                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st,
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+// Algorithmic FLOPs of one engine launch: per half sweep n (l k [Y = U M] +
+// k^2 [column updates] + l k [U^T F] + k (k + 1) / 2 [F^T F]) FMAs, plus the
+// prologue's n (l k + k (k + 1) / 2); two FLOPs per FMA.
+double lai_engine_flops(int64_t n, int k, int l, int nsweeps);
 
 // -------------------------------------------------------------- CholeskyQR3
 // Shifted CholeskyQR3 of S (n x l, l <= 96) in place; T is n x l scratch for

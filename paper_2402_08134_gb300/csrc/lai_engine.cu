@@ -764,8 +764,15 @@ static size_t smem_optin_limit() {
   return v > 1024 ? (size_t)(v - 1024) : 0;  // room for the kernels' static shared memory
 }
 
+double lai_engine_flops(int64_t n, int k, int l, int nsweeps) {
+  const double half = (double)n * ((double)l * k + (double)k * k + (double)l * k + 0.5 * k * (k + 1));
+  const double pro = (double)n * ((double)l * k + 0.5 * k * (k + 1));
+  return 2.0 * (pro + 2.0 * nsweeps * half);
+}
+
 template <int KMAX>
-static cudaError_t launch_engine(LaiArgs a, bool allow_resident, cudaStream_t st) {
+static cudaError_t launch_engine(LaiArgs a, bool allow_resident, cudaStream_t st, cudaEvent_t ev0,
+                                 cudaEvent_t ev1) {
   int grid = num_sms();
   if ((int64_t)grid > a.n) grid = (int)std::max<int64_t>(1, a.n);
   const int64_t rmax = (a.n + grid - 1) / grid;
@@ -790,14 +797,17 @@ static cudaError_t launch_engine(LaiArgs a, bool allow_resident, cudaStream_t st
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   void* params[] = {&a};
+  if (ev0 && (e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(LE_THREADS), params, smem, st);
   count_launches(1);
+  if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, st);
   return e;
 }
 
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
-                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st) {
+                       double* Gout, unsigned* err, bool allow_resident, cudaStream_t st, cudaEvent_t ev0,
+                       cudaEvent_t ev1) {
   if (k < 1 || k > 64 || l < 1 || l > 96 || n < 1 || nsweeps > obj_cap) return cudaErrorInvalidValue;
   char* b = static_cast<char*>(ws);
   const size_t grid = (size_t)num_sms();
@@ -818,12 +828,12 @@ cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, in
   // the state's pad entries are never written by the kernel
   e = cudaMemsetAsync(state, 0, (size_t)2 * le_state_floats(l, k, gp) * sizeof(float), st);
   if (e != cudaSuccess) return e;
-  if (k <= 8) return launch_engine<8>(a, allow_resident, st);
-  if (k <= 16) return launch_engine<16>(a, allow_resident, st);
-  if (k <= 24) return launch_engine<24>(a, allow_resident, st);
-  if (k <= 32) return launch_engine<32>(a, allow_resident, st);
-  if (k <= 48) return launch_engine<48>(a, allow_resident, st);
-  return launch_engine<64>(a, allow_resident, st);
+  if (k <= 8) return launch_engine<8>(a, allow_resident, st, ev0, ev1);
+  if (k <= 16) return launch_engine<16>(a, allow_resident, st, ev0, ev1);
+  if (k <= 24) return launch_engine<24>(a, allow_resident, st, ev0, ev1);
+  if (k <= 32) return launch_engine<32>(a, allow_resident, st, ev0, ev1);
+  if (k <= 48) return launch_engine<48>(a, allow_resident, st, ev0, ev1);
+  return launch_engine<64>(a, allow_resident, st, ev0, ev1);
 }
 
 }  // namespace symnmf
