@@ -69,6 +69,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest `value` over all ranks (the step time every rank reports is the slowest one)."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ clocks
 
 
@@ -267,10 +278,7 @@ def run_ours(args):
     s.profile(False)
     launches = S.launch_count() - launches0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, world, dev)
 
     # verification against the oracle's residual (untimed)
     nr_true = s.residual(S.SRC_XHI)[0]
