@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP8 and batched forms")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch sweep kernels one by one instead of replaying recorded graphs (for profilers)")
     return ap.parse_args()
@@ -191,6 +192,67 @@ def fp32_peak_tflops(dev, clk):
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
+def batched_form(S, dev, sweeps=100, sample_every=8):
+    """The batched grouped solver on 64 dense SBM problems x 4 restarts (one grouped launch per sweep,
+    graph replay), and the plain FP32 form solving a sample of the same problems one restart at a time."""
+    import torch
+
+    from synth import batched_problem_specs
+
+    specs = batched_problem_specs(64, seed=0)
+    Xs, Xf = [], []
+    for p, sp in enumerate(specs):
+        m, kc = sp["n"], sp["k"]
+        g = torch.Generator(device=dev).manual_seed(1000 + p)
+        lab = torch.randperm(m, generator=g, device=dev) * kc // m
+        P = torch.where(lab[:, None] == lab[None, :], 0.3, 0.015)
+        A = torch.triu(torch.rand((m, m), generator=g, device=dev) < P, 1)
+        A = A | A.T
+        A.fill_diagonal_(True)
+        ld = (m + 7) // 8 * 8
+        buf = torch.zeros((m, ld), dtype=torch.bfloat16, device=dev)
+        buf[:, :m] = A.to(torch.bfloat16)
+        Xs.append(buf)
+        Xf.append(A.to(torch.float32) if p % sample_every == 0 else None)
+        del A, P
+    b = S.Batch(Xs, [sp["k"] for sp in specs], restarts=4)
+    b.init_random(True)
+    b.sweep(2, record=False)  # records the sweep graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.init_random(True)
+    b.sweep(sweeps, record=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    b.close()
+    # plain FP32 form: one solver per (problem, restart), full X every sweep, on every `sample_every`-th problem
+    t_p, solves = 0.0, 0
+    for p, sp in enumerate(specs):
+        if Xf[p] is None:
+            continue
+        for r in range(4):
+            sv = S.Solver(Xf[p], sp["k"], seed=1 + r)
+            sv.init_random(True)
+            sv.sweep(1, record=False)
+            torch.cuda.synchronize()
+            e0.record()
+            sv.init_random(True)
+            sv.sweep(sweeps, record=False)
+            e1.record()
+            torch.cuda.synchronize()
+            t_p += e0.elapsed_time(e1) / 1e3
+            solves += 1
+            sv.close()
+    scale = (64 * 4) / max(solves, 1)
+    return {"s": t_b, "solves": 256, "sweeps": sweeps, "dtype": "bf16",
+            "plain_fp32_sequential_s": t_p * scale,
+            "plain_sample": f"{solves} of the 256 solves (every {sample_every}th problem, all restarts), "
+                            f"scaled x{scale:.1f}",
+            "speedup_vs_plain": (t_p * scale) / t_b if t_b > 0 else None}
+
+
 # --------------------------------------------------------------- oracle side
 
 
@@ -304,6 +366,34 @@ def run_ours(args):
                              "ok_vs_oracle": (abs(nr_plain - gold["plain_nr"]) <= 1e-4 * gold["plain_nr"])
                              if gold else None}
         sp.close()
+
+    if not args.no_forms:
+        # FP8 form of the same solve: X as E4M3 with per-row scales for the sketch and the LAI sweeps,
+        # the FP32 copy for the refinement sweeps
+        x8, rs8 = S.quantize_fp8(Xf)
+        s8 = S.Solver(x8, K, row_scale=rs8, max_width=L, seed=SEED, x_hi=Xf, use_graph=not args.no_graph)
+
+        def step8():
+            s8.init_random(True)
+            s8.lai_sketch(L, Q)
+            s8.sweep(SWEEPS, source=S.SRC_LAI, record=False)
+            s8.sweep(N_REFINE, source=S.SRC_X, record=False)
+            return s8.residual(S.SRC_X)[0]
+
+        step8()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step8()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out["fp8"] = {"s": a.elapsed_time(b) / 1e3 / args.steps, "nr": s8.residual(S.SRC_XHI)[0],
+                      "reached_target": (s8.residual(S.SRC_XHI)[0] <= target) if target else None}
+        s8.close()
+        del x8, rs8
+        out["batched_c4"] = batched_form(S, dev)
 
     # end to end through the public API: X from pinned host memory, result back to host
     Xh = Xb.cpu().pin_memory()

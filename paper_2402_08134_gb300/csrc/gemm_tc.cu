@@ -6,8 +6,11 @@
 //
 // Layout: A = X (n x n, K-major rows, TMA tiles 128 x 128 bytes, 128-byte
 // swizzle), B = F^T packed (BN x n, K-major, same swizzle), D = 128 x BN FP32
-// in TMEM.  Warp roles per CTA (192 threads, one CTA per SM):
-//   warp 0      : TMA producer (one thread) into an STAGES-deep smem ring;
+// in TMEM.  Warp roles per CTA (224 threads, one CTA per SM):
+//   warp 0      : TMA producer of A (one thread) into its own smem ring;
+//   warp 6      : TMA producer of B (one thread) into a second, shallower ring
+//                 (F is re-read by every CTA and comes from L2; X streams from
+//                 HBM and needs the deeper buffering);
 //   warp 1      : TMEM allocator + MMA issuer (one thread);
 //   warps 2..5  : epilogue, tcgen05.ld of the accumulator -> FP32 partials.
 // Two TMEM accumulators alternate so that the epilogue of one tile overlaps
@@ -33,23 +36,26 @@
 
 namespace symnmf {
 
+constexpr int XF_THREADS = 224;  // warps 0..6: A producer, MMA, 4 epilogue warps, B producer
+
 template <int BN>
 struct TcCfg {
   static constexpr int A_BYTES = TC_BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (196 * 1024 / STAGE_BYTES) > 8 ? 8 : (196 * 1024 / STAGE_BYTES);
+  static constexpr int B_STAGES = 4;
+  static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
+  static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
   static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
 };
 
 template <int BN, bool FP8>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(XF_THREADS, 1)
     xf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int kblocks, int64_t total_iters, float* __restrict__ partials, int max_segs,
                  unsigned* err) {
   using C = TcCfg<BN>;
-  constexpr int STAGES = C::STAGES;
+  constexpr int SA = C::A_STAGES, SB = C::B_STAGES;
   constexpr int KSTEPS = TC_ROW_BYTES / 32;  // 32 bytes of K per MMA (16 bf16 / 32 e4m3)
   constexpr int KELEMS = FP8 ? 128 : 64;     // elements of K per k block
   constexpr uint32_t IDESC = make_idesc<FP8>(TC_BM, BN);
@@ -57,10 +63,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * C::A_BYTES;
-  uint64_t* full = (uint64_t*)(sB + STAGES * C::B_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint8_t* sB = smem + SA * C::A_BYTES;
+  uint64_t* fullA = (uint64_t*)(sB + SB * C::B_BYTES);
+  uint64_t* emptyA = fullA + SA;
+  uint64_t* fullB = emptyA + SA;
+  uint64_t* emptyB = fullB + SB;
+  uint64_t* tfull = emptyB + SB;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -71,9 +79,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int64_t it1 = ((int64_t)(blockIdx.x + 1) * total_iters) / gridDim.x;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int s = 0; s < SA; ++s) {
+      mbar_init(&fullA[s], 1);
+      mbar_init(&emptyA[s], 1);
+    }
+    for (int s = 0; s < SB; ++s) {
+      mbar_init(&fullB[s], 1);
+      mbar_init(&emptyB[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -96,9 +108,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == 0) {
+  if (warp == 0 || warp == 6) {
     if (lane == 0) {
-      // ---------------- producer
+      // ---------------- producers: warp 0 streams A (X row tiles), warp 6 streams B (F^T)
+      const bool isA = warp == 0;
+      const int S = isA ? SA : SB;
+      uint64_t* fullR = isA ? fullA : fullB;
+      uint64_t* emptyR = isA ? emptyA : emptyB;
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued_mask = 0;   // stages used at least once
@@ -106,33 +122,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int64_t it = it0; it < it1; ++it) {
         const int tile = (int)(it / kblocks);
         const int kb = (int)(it - (int64_t)tile * kblocks);
-        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+        if (!mbar_wait(&emptyR[stage], phase ^ 1u, abort_flag)) {
           *abort_flag = 1;
           set_error(err, ERR_TIMEOUT);
           break;
         }
-        mbar_expect_tx(&full[stage], C::STAGE_BYTES);
-        tma_load_2d(sA + stage * C::A_BYTES, &tmA, kb * KELEMS, tile * TC_BM, &full[stage]);
-        tma_load_2d(sB + stage * C::B_BYTES, &tmB, kb * KELEMS, 0, &full[stage]);
+        if (isA) {
+          mbar_expect_tx(&fullR[stage], C::A_BYTES);
+          tma_load_2d(sA + stage * C::A_BYTES, &tmA, kb * KELEMS, tile * TC_BM, &fullR[stage]);
+        } else {
+          mbar_expect_tx(&fullR[stage], C::B_BYTES);
+          tma_load_2d(sB + stage * C::B_BYTES, &tmB, kb * KELEMS, 0, &fullR[stage]);
+        }
         issued_mask |= 1u << stage;
         last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
-        if (++stage == STAGES) {
+        if (++stage == S) {
           stage = 0;
           phase ^= 1u;
         }
       }
       // drain: every copy this thread issued has landed before the CTA exits
-      for (int s = 0; s < STAGES; ++s)
+      for (int s = 0; s < S; ++s)
         if (issued_mask >> s & 1u) {
           volatile int no_abort = 0;
-          mbar_wait(&full[s], (last_parity >> s) & 1u, &no_abort);
+          mbar_wait(&fullR[s], (last_parity >> s) & 1u, &no_abort);
         }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      int stage = 0;
-      uint32_t phase = 0;
+      int sa = 0, sb = 0;
+      uint32_t pa = 0, pb = 0;
       int seg = 0;
       bool ok = true;
       int64_t it = it0;
@@ -149,21 +169,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t d = tmem_base + (uint32_t)(a * BN);
         const int64_t seg_begin = it;
         for (; it < seg_end; ++it) {
-          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          if (!mbar_wait(&fullA[sa], pa, abort_flag) || !mbar_wait(&fullB[sb], pb, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sA + stage * C::A_BYTES);
-          const uint32_t b0 = smem_u32(sB + stage * C::B_BYTES);
+          const uint32_t a0 = smem_u32(sA + sa * C::A_BYTES);
+          const uint32_t b0 = smem_u32(sB + sb * C::B_BYTES);
 #pragma unroll
           for (int ks = 0; ks < KSTEPS; ++ks)
             umma<FP8>(d, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), IDESC,
                       (it > seg_begin || ks > 0) ? 1u : 0u);
-          umma_commit(&empty[stage]);
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
+          umma_commit(&emptyA[sa]);
+          umma_commit(&emptyB[sb]);
+          if (++sa == SA) {
+            sa = 0;
+            pa ^= 1u;
+          }
+          if (++sb == SB) {
+            sb = 0;
+            pb ^= 1u;
           }
         }
         if (!ok) break;
@@ -224,25 +249,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // Y[r, c] = (sum over the CTAs that covered row tile r / 128 of their partial)
 //           * row_scale[r] * col_scale[c]  (scales for FP8 only).
-__global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN,
-                                 int64_t kblocks, int64_t total, int G, int64_t n, int N, float* Y,
-                                 int ldy, const float* __restrict__ rs, const float* __restrict__ cs) {
+__global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN, int kblocks,
+                                 int64_t total, int G, int64_t n, int N, float* Y, int ldy,
+                                 const float* __restrict__ rs, const float* __restrict__ cs) {
+  // one thread per (row, 4 columns); the CTAs that covered the row's tile are
+  // c0..c1 (stream-K ranges are contiguous), CTA q's segment index for the tile
+  // is tile - (first tile of q)
+  const int nq = (N + 3) >> 2;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * N) return;
-  const int64_t r = t / N;
-  const int c = (int)(t - r * N);
+  if (t >= n * nq) return;
+  const int64_t r = t / nq;
+  const int c = (int)(t - r * nq) * 4;
   const int64_t tile = r / TC_BM;
+  const int rr = (int)(r - tile * TC_BM);
   const int64_t f_it = tile * kblocks, l_it = (tile + 1) * kblocks - 1;
   const int64_t c0 = ((f_it + 1) * G - 1) / total;
   const int64_t c1 = ((l_it + 1) * G - 1) / total;
-  float s = 0.f;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t q = c0; q <= c1; ++q) {
-    const int64_t itb = (q * total) / G;
-    const int64_t seg = tile - itb / kblocks;
-    s += partials[((q * max_segs + seg) * TC_BM + (r - tile * TC_BM)) * BN + c];
+    const int64_t first_tile = ((q * total) / G) / kblocks;
+    const int seg = (int)(tile - first_tile);
+    const float4 v = *reinterpret_cast<const float4*>(partials + (((q * max_segs + seg) * TC_BM + rr) * BN + c));
+    s.x += v.x;
+    s.y += v.y;
+    s.z += v.z;
+    s.w += v.w;
   }
-  if (rs) s *= rs[r] * cs[c];
-  Y[r * ldy + c] = s;
+  const float sv[4] = {s.x, s.y, s.z, s.w};
+  const float rsr = rs ? rs[r] : 1.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (c + u < N) Y[r * ldy + c + u] = rs ? sv[u] * rsr * cs[c + u] : sv[u];
 }
 
 // ------------------------------------------------------------ host side
@@ -311,20 +348,30 @@ size_t xf_tc_ws_floats(int64_t n, int BN) {
   return (size_t)p.G * segs * TC_BM * BN;
 }
 
+// Fpack[c, i] = F[i, c] (zero padded to Npad x ldp) through 32 x 32 tiles in
+// shared memory: both the reads of F rows and the writes of Fpack rows coalesce.
 __global__ void pack_ft_bf16_kernel(const float* F, int64_t n, int ldf, int N, int Npad,
                                     __nv_bfloat16* out, int64_t ldp) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)Npad * ldp) return;
-  const int64_t c = t / ldp, i = t - c * ldp;
-  const float v = (c < N && i < n) ? F[i * ldf + c] : 0.f;
-  out[t] = __float2bfloat16_rn(v);
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t i = i0 + y;
+    const int c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (i < n && c < N) ? F[i * ldf + c] : 0.f;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y;
+    const int64_t i = i0 + threadIdx.x;
+    if (c < Npad && i < ldp) out[(int64_t)c * ldp + i] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
 }
 
 cudaError_t pack_ft_bf16(const float* F, int64_t n, int ldf, int N, int Npad, void* out, int64_t ldp,
                          cudaStream_t st) {
-  const int64_t work = (int64_t)Npad * ldp;
-  pack_ft_bf16_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(F, n, ldf, N, Npad,
-                                                                 (__nv_bfloat16*)out, ldp);
+  const dim3 grid((unsigned)((ldp + 31) / 32), (unsigned)((Npad + 31) / 32));
+  pack_ft_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(F, n, ldf, N, Npad, (__nv_bfloat16*)out, ldp);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -372,7 +419,7 @@ static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const
   cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        C::SMEM);
   if (e != cudaSuccess) return e;
-  xf_tc_kernel<BN, FP8><<<p.G, TC_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  xf_tc_kernel<BN, FP8><<<p.G, XF_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -416,7 +463,7 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   }
   if (ev_end) cudaEventRecord(ev_end, st);
   if (e != cudaSuccess) return e;
-  const int64_t work = n * N;
+  const int64_t work = n * ((N + 3) / 4);
   tc_reduce_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(
       ws, p.max_segs, BN, p.kblocks, p.total, p.G, n, N, Y, ldy, fp8 ? row_scale : nullptr,
       fp8 ? col_scale : nullptr);
