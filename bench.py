@@ -392,7 +392,26 @@ def run_ours(args):
         out["fp8"] = {"s": a.elapsed_time(b) / 1e3 / args.steps, "nr": s8.residual(S.SRC_XHI)[0],
                       "reached_target": (s8.residual(S.SRC_XHI)[0] <= target) if target else None}
         s8.close()
-        del x8, rs8
+        # the product kernel at a width past the BF16 ridge (N = 256, 256 flop per byte of BF16 X),
+        # timed alone (kernel events), against the measured burst peak of its dtype
+        pk_t, _ = peaks()
+        Fw = torch.rand((N, 256), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        tens = {}
+        for name, fn, peak in (("bf16", lambda: S.dense_xf(Xb, Fw, gemm=S.GEMM_TC), pk_t["bf16_tflops"]),
+                               ("fp8", lambda: S.dense_xf(x8, Fw, row_scale=rs8, gemm=S.GEMM_TC),
+                                2.0 * pk_t["bf16_tflops"])):
+            fn()
+            torch.cuda.synchronize()
+            S.profile_standalone(True)
+            for _ in range(10):
+                fn()
+            t_ms, nl, fl, _ = S.profile_standalone_read()
+            S.profile_standalone(False)
+            tf = fl / (t_ms * 1e-3) / 1e12
+            tens[name] = {"tflops": tf, "peak_tflops": peak, "frac": tf / peak, "kernel_ms": t_ms / nl,
+                          "peak_kind": "measured burst" if name == "bf16" else "measured BF16 burst x 2 (nominal ratio)"}
+        out["tensor_n256"] = dict(tens, shape=f"n={N}, N=256 (xf_tc_kernel<256, 256-row tiles>)")
+        del x8, rs8, Fw
         out["batched_c4"] = batched_form(S, dev)
 
     # end to end through the public API: X from pinned host memory, result back to host

@@ -246,6 +246,13 @@ symnmf_status symnmf_convert_bf16(const float* x, int64_t n, int64_t ldx, uint16
  * bytes (X once, F and Y once each), then resets the record. */
 symnmf_status symnmf_profile(symnmf_t h, int enable);
 symnmf_status symnmf_profile_read(symnmf_t h, double* total_ms, int64_t* launches, double* bytes);
+/* Process-wide timing of the standalone tensor-core products (symnmf_dense_xf
+ * with X in BF16 or FP8): while enabled, the product kernel of every call is
+ * bracketed by CUDA events; the read returns the summed kernel time (ms), the
+ * number of launches, their FLOPs (2 n^2 N each) and algorithmic bytes (X
+ * once, F and Y once), then resets the record.  Thread-safe. */
+symnmf_status symnmf_profile_standalone(int enable);
+symnmf_status symnmf_profile_standalone_read(double* total_ms, int64_t* launches, double* flops, double* bytes);
 /* The same for the persistent LAI-HALS sweep launches (Alg. LAI-SymNMF loop):
  * summed kernel time (ms), number of launches and their algorithmic FLOPs --
  * per half sweep n (l k + k^2 + l k + k (k + 1) / 2) FMAs (Y = U M, the column

@@ -95,6 +95,8 @@ _SIGS = {
     "symnmf_profile": (_I, [_P, _I]),
     "symnmf_profile_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
     "symnmf_profile_read_engine": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
+    "symnmf_profile_standalone": (_I, [_I]),
+    "symnmf_profile_standalone_read": (_I, [_DP, C.POINTER(C.c_int64), _DP, _DP]),
     "symnmf_batched_create": (_I, [C.POINTER(symnmf_problem), _I, _I, C.POINTER(symnmf_options), _P,
                                    C.POINTER(_P)]),
     "symnmf_batched_destroy": (None, [_P]),
@@ -492,6 +494,18 @@ def csr_xf(row_ptr, col, val, F, stream=None):
     Y = torch.empty((n, N), dtype=torch.float32, device=F.device)
     check(symnmf_csr_xf(_ptr(row_ptr), _ptr(col), _ptr(val), n, _ptr(F), N, _ptr(Y), _stream(stream)))
     return Y
+
+
+def profile_standalone(enable=True):
+    """Time the kernel of every standalone tensor-core product (dense_xf) with CUDA events."""
+    check(symnmf_profile_standalone(1 if enable else 0))
+
+
+def profile_standalone_read():
+    """(total kernel ms, launches, FLOPs, algorithmic bytes) since the last read; resets the record."""
+    t, n, f, b = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+    check(symnmf_profile_standalone_read(C.byref(t), C.byref(n), C.byref(f), C.byref(b)))
+    return t.value, n.value, f.value, b.value
 
 
 def gram(F, stream=None):

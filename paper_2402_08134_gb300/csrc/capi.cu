@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -816,6 +817,65 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
 
 // ------------------------------------------------------- standalone kernels
 
+// Process-wide event timing of standalone tensor-core products (symnmf_dense_xf).
+namespace {
+std::mutex g_sprof_mu;
+bool g_sprof_on = false;
+size_t g_sprof_used = 0;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_sprof_ev;
+std::vector<double> g_sprof_flops, g_sprof_bytes;
+}  // namespace
+
+// Events for the next standalone product when profiling is on (nullptr otherwise).
+static cudaError_t standalone_events(cudaEvent_t* e0, cudaEvent_t* e1, double flops, double bytes) {
+  std::lock_guard<std::mutex> lock(g_sprof_mu);
+  *e0 = *e1 = nullptr;
+  if (!g_sprof_on) return cudaSuccess;
+  if (g_sprof_used == g_sprof_ev.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) return e;
+    g_sprof_ev.push_back({a, b});
+    g_sprof_flops.push_back(0.0);
+    g_sprof_bytes.push_back(0.0);
+  }
+  *e0 = g_sprof_ev[g_sprof_used].first;
+  *e1 = g_sprof_ev[g_sprof_used].second;
+  g_sprof_flops[g_sprof_used] = flops;
+  g_sprof_bytes[g_sprof_used] = bytes;
+  g_sprof_used++;
+  return cudaSuccess;
+}
+
+extern "C" symnmf_status symnmf_profile_standalone(int enable) {
+  std::lock_guard<std::mutex> lock(g_sprof_mu);
+  g_sprof_on = enable != 0;
+  g_sprof_used = 0;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_profile_standalone_read(double* total_ms, int64_t* launches, double* flops,
+                                                        double* bytes) {
+  std::lock_guard<std::mutex> lock(g_sprof_mu);
+  double t = 0.0, fl = 0.0, by = 0.0;
+  for (size_t i = 0; i < g_sprof_used; ++i) {
+    cudaError_t e = cudaEventSynchronize(g_sprof_ev[i].second);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, g_sprof_ev[i].first, g_sprof_ev[i].second);
+    if (e != cudaSuccess) return to_status(e);
+    t += ms;
+    fl += g_sprof_flops[i];
+    by += g_sprof_bytes[i];
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = (int64_t)g_sprof_used;
+  if (flops) *flops = fl;
+  if (bytes) *bytes = by;
+  g_sprof_used = 0;
+  return SYMNMF_OK;
+}
+
 extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, const float* row_scale,
                                          int64_t n, const float* F, int ldf, int N, float* Y, int ldy,
                                          int gemm, void* stream) {
@@ -852,7 +912,10 @@ extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, co
     e = pack_ft_bf16(F, n, ldf, N, BN, pack, ldp, st);
   else
     e = pack_ft_fp8(F, n, ldf, N, BN, pack, ldp, cs, st);
-  if (e == cudaSuccess) e = xf_tc(fmt, x, ldx, row_scale, n, pack, ldp, cs, N, Y, ldy, ws, wsf, err, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = standalone_events(&e0, &e1, 2.0 * n * n * N, (double)n * n * es + (double)n * N * (es + 4.0));
+  if (e == cudaSuccess)
+    e = xf_tc(fmt, x, ldx, row_scale, n, pack, ldp, cs, N, Y, ldy, ws, wsf, err, st, e0, e1);
   unsigned herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

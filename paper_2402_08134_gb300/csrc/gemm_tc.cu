@@ -38,23 +38,29 @@ namespace symnmf {
 
 constexpr int XF_THREADS = 224;  // warps 0..6: A producer, MMA, 4 epilogue warps, B producer
 
-template <int BN>
+// M2: a CTA's row tile is 256 rows (two 128-row MMA halves sharing every F
+// stage, accumulators in TMEM columns [0, BN) and [BN, 2 BN), one buffer);
+// otherwise 128 rows with two alternating accumulators.
+template <int BN, bool M2 = false>
 struct TcCfg {
-  static constexpr int A_BYTES = TC_BM * TC_ROW_BYTES;
+  static constexpr int BM = M2 ? 2 * TC_BM : TC_BM;
+  static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
-  static constexpr int B_STAGES = 4;
+  static constexpr int B_STAGES = M2 ? 3 : 4;
   static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
+  static constexpr int NBUF = M2 ? 1 : 2;  // accumulator buffers in TMEM
   static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
   static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
 };
 
-template <int BN, bool FP8>
+template <int BN, bool FP8, bool M2 = false>
 __global__ void __launch_bounds__(XF_THREADS, 1)
     xf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int kblocks, int64_t total_iters, float* __restrict__ partials, int max_segs,
                  unsigned* err) {
-  using C = TcCfg<BN>;
+  using C = TcCfg<BN, M2>;
+  constexpr int BM = C::BM, NBUF = C::NBUF;
   constexpr int SA = C::A_STAGES, SB = C::B_STAGES;
   constexpr int KSTEPS = TC_ROW_BYTES / 32;  // 32 bytes of K per MMA (16 bf16 / 32 e4m3)
   constexpr int KELEMS = FP8 ? 128 : 64;     // elements of K per k block
@@ -129,7 +135,10 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
         }
         if (isA) {
           mbar_expect_tx(&fullR[stage], C::A_BYTES);
-          tma_load_2d(sA + stage * C::A_BYTES, &tmA, kb * KELEMS, tile * TC_BM, &fullR[stage]);
+#pragma unroll
+          for (int h = 0; h < BM / TC_BM; ++h)
+            tma_load_2d(sA + stage * C::A_BYTES + h * TC_BM * TC_ROW_BYTES, &tmA, kb * KELEMS,
+                        tile * BM + h * TC_BM, &fullR[stage]);
         } else {
           mbar_expect_tx(&fullR[stage], C::B_BYTES);
           tma_load_2d(sB + stage * C::B_BYTES, &tmB, kb * KELEMS, 0, &fullR[stage]);
@@ -159,8 +168,8 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
       while (ok && it < it1) {
         const int64_t tile = it / kblocks;
         const int64_t seg_end = min(it1, (tile + 1) * kblocks);
-        const int a = seg & 1;
-        const uint32_t use = (uint32_t)(seg >> 1);
+        const int a = seg % NBUF;
+        const uint32_t use = (uint32_t)(seg / NBUF);
         if (!mbar_wait(&tempty[a], (use & 1u) ^ 1u, abort_flag)) {
           ok = false;
           break;
@@ -177,9 +186,11 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
           const uint32_t a0 = smem_u32(sA + sa * C::A_BYTES);
           const uint32_t b0 = smem_u32(sB + sb * C::B_BYTES);
 #pragma unroll
-          for (int ks = 0; ks < KSTEPS; ++ks)
-            umma<FP8>(d, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), IDESC,
-                      (it > seg_begin || ks > 0) ? 1u : 0u);
+          for (int h = 0; h < BM / TC_BM; ++h)
+#pragma unroll
+            for (int ks = 0; ks < KSTEPS; ++ks)
+              umma<FP8>(d + (uint32_t)(h * BN), sw128_desc(a0 + h * TC_BM * TC_ROW_BYTES + ks * 32),
+                        sw128_desc(b0 + ks * 32), IDESC, (it > seg_begin || ks > 0) ? 1u : 0u);
           umma_commit(&emptyA[sa]);
           umma_commit(&emptyB[sb]);
           if (++sa == SA) {
@@ -207,29 +218,32 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
   } else {
     // ---------------- epilogue (warps 2..5)
     const int ew = warp & 3;
-    const int row = ew * 32 + lane;
     int seg = 0;
     int64_t it = it0;
     while (it < it1) {
       const int64_t tile = it / kblocks;
       const int64_t seg_end = min(it1, (tile + 1) * kblocks);
-      const int a = seg & 1;
-      const uint32_t use = (uint32_t)(seg >> 1);
+      const int a = seg % NBUF;
+      const uint32_t use = (uint32_t)(seg / NBUF);
       if (!mbar_wait(&tfull[a], use & 1u, abort_flag)) {
         *abort_flag = 1;
         set_error(err, ERR_TIMEOUT);
         break;
       }
       tc_fence_after();
-      float* dst = partials + (((size_t)blockIdx.x * max_segs + seg) * TC_BM + row) * BN;
-      const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
-        float v[16];
-        tmem_ld16(taddr + (uint32_t)c, v);
+      for (int h = 0; h < BM / TC_BM; ++h) {
+        const int row = h * TC_BM + ew * 32 + lane;
+        float* dst = partials + (((size_t)blockIdx.x * max_segs + seg) * BM + row) * BN;
+        const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16) + (uint32_t)((a + h) * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)c, v);
 #pragma unroll
-        for (int q = 0; q < 16; q += 4)
-          *(float4*)(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          for (int q = 0; q < 16; q += 4)
+            *(float4*)(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
 
 // Y[r, c] = (sum over the CTAs that covered row tile r / 128 of their partial)
 //           * row_scale[r] * col_scale[c]  (scales for FP8 only).
-__global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN, int kblocks,
+__global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN, int BM, int kblocks,
                                  int64_t total, int G, int64_t n, int N, float* Y, int ldy,
                                  const float* __restrict__ rs, const float* __restrict__ cs) {
   // one thread per (row, 4 columns); the CTAs that covered the row's tile are
@@ -260,8 +274,8 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_seg
   if (t >= n * nq) return;
   const int64_t r = t / nq;
   const int c = (int)(t - r * nq) * 4;
-  const int64_t tile = r / TC_BM;
-  const int rr = (int)(r - tile * TC_BM);
+  const int64_t tile = r / BM;
+  const int rr = (int)(r - tile * BM);
   const int64_t f_it = tile * kblocks, l_it = (tile + 1) * kblocks - 1;
   const int64_t c0 = ((f_it + 1) * G - 1) / total;
   const int64_t c1 = ((l_it + 1) * G - 1) / total;
@@ -269,7 +283,7 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_seg
   for (int64_t q = c0; q <= c1; ++q) {
     const int64_t first_tile = ((q * total) / G) / kblocks;
     const int seg = (int)(tile - first_tile);
-    const float4 v = *reinterpret_cast<const float4*>(partials + (((q * max_segs + seg) * TC_BM + rr) * BN + c));
+    const float4 v = *reinterpret_cast<const float4*>(partials + (((q * max_segs + seg) * BM + rr) * BN + c));
     s.x += v.x;
     s.y += v.y;
     s.z += v.z;
@@ -320,15 +334,20 @@ int tc_block_n(int N) {
 }
 
 struct TcPlan {
-  int G, kblocks, mtiles, max_segs;
+  int G, kblocks, mtiles, max_segs, bm;
   int64_t total;
 };
 
-static TcPlan tc_plan(int64_t n, bool fp8) {
+// Row tiles of 256 (two MMA halves sharing each F stage) for the widest
+// products, where F's traffic from L2 would otherwise limit the tensor rate.
+static bool tc_m2(int N) { return N > 128; }
+
+static TcPlan tc_plan(int64_t n, bool fp8, int bm = TC_BM) {
   TcPlan p;
   const int kel = fp8 ? 128 : 64;
+  p.bm = bm;
   p.kblocks = (int)((n + kel - 1) / kel);
-  p.mtiles = (int)((n + TC_BM - 1) / TC_BM);
+  p.mtiles = (int)((n + bm - 1) / bm);
   p.total = (int64_t)p.kblocks * p.mtiles;
   p.G = (int)std::min<int64_t>(num_sms(), p.total);
   p.max_segs = 1;
@@ -341,11 +360,14 @@ static TcPlan tc_plan(int64_t n, bool fp8) {
 }
 
 size_t xf_tc_ws_floats(int64_t n, int BN) {
-  // the BF16 plan has the most k blocks, hence the most segments
-  const TcPlan p = tc_plan(n, false);
-  const TcPlan q = tc_plan(n, true);
-  const int segs = p.max_segs > q.max_segs ? p.max_segs : q.max_segs;
-  return (size_t)p.G * segs * TC_BM * BN;
+  // largest of the plans a product of this width can use
+  const int bm = tc_m2(BN) ? 2 * TC_BM : TC_BM;
+  size_t need = 0;
+  for (int f = 0; f < 2; ++f) {
+    const TcPlan p = tc_plan(n, f != 0, bm);
+    need = std::max(need, (size_t)p.G * p.max_segs * bm * BN);
+  }
+  return need;
 }
 
 // Fpack[c, i] = F[i, c] (zero padded to Npad x ldp) through 32 x 32 tiles in
@@ -412,14 +434,14 @@ cudaError_t pack_ft_fp8(const float* F, int64_t n, int ldf, int N, int Npad, voi
   return cudaGetLastError();
 }
 
-template <int BN, bool FP8>
+template <int BN, bool FP8, bool M2 = false>
 static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
                              unsigned* err, cudaStream_t st) {
-  using C = TcCfg<BN>;
-  cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = TcCfg<BN, M2>;
+  cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8, M2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        C::SMEM);
   if (e != cudaSuccess) return e;
-  xf_tc_kernel<BN, FP8><<<p.G, XF_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  xf_tc_kernel<BN, FP8, M2><<<p.G, XF_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -436,8 +458,9 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   // TMA: 16-byte aligned bases and row pitches
   if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
     return cudaErrorInvalidValue;
-  const TcPlan p = tc_plan(n, fp8);
-  if (ws_floats < (size_t)p.G * p.max_segs * TC_BM * BN) return cudaErrorInvalidValue;
+  const bool m2 = tc_m2(N);
+  const TcPlan p = tc_plan(n, fp8, m2 ? 2 * TC_BM : TC_BM);
+  if (ws_floats < (size_t)p.G * p.max_segs * p.bm * BN) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   const uint32_t kel = fp8 ? 128 : 64;
   if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)n, (uint64_t)ldx * es, kel, TC_BM))
@@ -451,21 +474,21 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
       case 32: e = launch_tc<32, true>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, true>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<256, true>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<256, true, true>(ma, mb, p, ws, err, st); break;
     }
   } else {
     switch (BN) {
       case 32: e = launch_tc<32, false>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, false>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, false>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<256, false>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<256, false, true>(ma, mb, p, ws, err, st); break;
     }
   }
   if (ev_end) cudaEventRecord(ev_end, st);
   if (e != cudaSuccess) return e;
   const int64_t work = n * ((N + 3) / 4);
   tc_reduce_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(
-      ws, p.max_segs, BN, p.kblocks, p.total, p.G, n, N, Y, ldy, fp8 ? row_scale : nullptr,
+      ws, p.max_segs, BN, p.bm, p.kblocks, p.total, p.G, n, N, Y, ldy, fp8 ? row_scale : nullptr,
       fp8 ? col_scale : nullptr);
   count_launches(1);
   return cudaGetLastError();

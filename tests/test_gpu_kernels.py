@@ -40,7 +40,7 @@ def test_simt_product_f32_and_f64(S, n, N):
 
 
 @pytest.mark.parametrize("n", [1000, 4104, 20000])
-@pytest.mark.parametrize("N", [10, 20, 50, 64, 100, 200])
+@pytest.mark.parametrize("N", [10, 20, 50, 64, 100, 200, 256])  # > 128: 256-row tiles
 def test_tcgen05_bf16_product(S, n, N):
     if n == 20000 and N not in (20, 50):
         pytest.skip("full size only at the sketch widths")
@@ -61,7 +61,7 @@ def test_tcgen05_bf16_product(S, n, N):
     assert (np.abs(Y - ref) <= bound).all(), np.abs(Y - ref).max()
 
 
-@pytest.mark.parametrize("n,N", [(1000, 20), (2064, 50), (4096, 128)])
+@pytest.mark.parametrize("n,N", [(1000, 20), (2064, 50), (4096, 128), (3000, 256), (333, 160)])
 def test_tcgen05_fp8_product(S, n, N):
     rng = np.random.default_rng(n + N)
     X = _sym(n, n).astype(np.float32)
