@@ -198,7 +198,7 @@ static symnmf_status half_sweep(symnmf_t h, int side, int src, int rule) {
     Y = h->Y;
   }
   if (rule == SYMNMF_RULE_HALS)
-    TRY(hals_update(Fu, Ff, n, k, 1, h->Gf[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
+    TRY(hals_update(Fu, Ff, n, k, h->Gf[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
                     h->counters + 1, h->err, h->st));
   else
     TRY(bpp_rows(Fu, Ff, n, k, h->Gd[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
@@ -731,7 +731,7 @@ static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule) {
   TRY(xcross(Ff, k, k, Ff, k, k, h->sb.cap, h->sb.idx, h->sb.wt, h->sb.counts + 2, nullptr, 0.0, h->Gs_d,
              h->Gs_f, h->ws, h->counters + 5, h->st));
   if (rule == SYMNMF_RULE_HALS)
-    TRY(hals_update(Fu, Ff, n, k, 1, h->Gs_f, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART,
+    TRY(hals_update(Fu, Ff, n, k, h->Gs_f, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART,
                     h->ws, h->counters + 1, h->err, h->st));
   else
     TRY(bpp_rows(Fu, Ff, n, k, h->Gs_d, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART, h->ws,
@@ -943,7 +943,8 @@ extern "C" symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G
   if ((e = cudaMallocAsync((void**)&ws, wsd * 8, st)) != cudaSuccess) return to_status(e);
   if ((e = cudaMallocAsync((void**)&cnt, 4, st)) != cudaSuccess) return to_status(e);
   cudaMemsetAsync(cnt, 0, 4, st);
-  e = xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, cnt, st);
+  // two blocks per SM, as symnmf_gram_noalloc: both entry points sum in the same order
+  e = xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, cnt, st, 2);
   cudaFreeAsync(ws, st);
   cudaFreeAsync(cnt, st);
   return to_status(e);

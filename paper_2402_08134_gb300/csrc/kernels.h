@@ -52,23 +52,22 @@ cudaError_t dense_sampled_xf(int fmt, const void* X, int64_t ldx, int64_t n, con
 // C (la x lb, FP64, and optionally FP32 Cf) = scale_row(A)^T B over n rows, with
 // optional row gather idx/wt (count from *cnt when cnt != NULL), optional row
 // scaling of the result by lam (C[i, :] *= lam[i]), and optional + shift*I.
-// ws: xcross_ws_doubles() doubles; counter: one zeroed unsigned.
+// ws: xcross_ws_doubles() doubles (max_blocks_per_sm x SMs x la x lb block
+// partials); counter: one zeroed unsigned.
 size_t xcross_ws_doubles(int la, int lb);
 cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int lb, int64_t n,
                    const int32_t* idx, const float* wt, const int* cnt, const double* lam,
                    double shift, double* C, float* Cf, double* ws, unsigned* counter,
-                   cudaStream_t st);
+                   cudaStream_t st, int max_blocks_per_sm = 4);
 
 // HALS update of F_upd rows (Eq. symhals_update2) with Y either given (Y != NULL)
 // or computed as U M (U n x l, M l x k FP32).  G FP32 k x k (no alpha),
-// F_fix the fixed factor.  Accumulates FP64 partials: part[0] = sum F_new .* Y,
-// part[1] = ||F_new - F_fix||^2 (reduced into part[0..1] by the last block;
-// ws >= 2 * 2048 doubles, counter zeroed).  ngroups > 1: row = ngroups blocks
-// of k columns, each with its own G (G[g*k*k ...]).
-cudaError_t hals_update(float* F_upd, const float* F_fix, int64_t n, int k, int ngroups,
-                        const float* G, double alpha, const float* Y, int ldy, const float* U, int l,
-                        const float* M, double* part, double* ws, unsigned* counter, unsigned* err,
-                        cudaStream_t st);
+// F_fix the fixed factor, k <= 64.  Accumulates FP64 partials: part[0] = sum
+// F_new .* Y, part[1] = ||F_new - F_fix||^2 (reduced into part[0..1] by the
+// last block; ws >= 2 * 2048 doubles, counter zeroed).
+cudaError_t hals_update(float* F_upd, const float* F_fix, int64_t n, int k, const float* G, double alpha,
+                        const float* Y, int ldy, const float* U, int l, const float* M, double* part, double* ws,
+                        unsigned* counter, unsigned* err, cudaStream_t st);
 
 // out[i, j] = sum_c A[i, c] B[c, j], A n x la (lda), B la x lb (FP32 small, row-major).
 cudaError_t apply_small(const float* A, int lda, int la, const float* B, int lb, int64_t n,
@@ -107,8 +106,9 @@ cudaError_t check_factor(const float* F, int64_t count, unsigned* flags, cudaStr
 // Row normalisation: out[i, :] = in[i, :] / ||in[i, :]||.
 cudaError_t normalize_rows(const float* in, int64_t n, int l, float* out, cudaStream_t st);
 
-// --------------------------------------------------------- small FP64 dense
-// Cholesky of G + shift I (k <= 112): R upper, Rinv (FP64 and FP32 copies).
+// --------------------------------------------------------- small dense
+// Cholesky of G + shift I (k <= 96) in double-float: R upper, Rinv (FP64 and
+// FP32 copies).
 // drop_tol > 0: pivots <= drop_tol * max_diag give zero rows/cols in Rinv
 // (rank-safe mode); else such a pivot sets ERR_NOTSPD.
 cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,

@@ -50,6 +50,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "persist.cuh"
+#include "hals_row.cuh"
 
 namespace symnmf {
 
@@ -359,57 +360,6 @@ __device__ __forceinline__ void le_objective_sums(const LaiArgs& a, double* shd)
   }
 }
 
-// Column updates of one row (Eq. symhals_update2) given its y = U_r M: the
-// fixed row read through `fx_at(i)`, the row being updated through the
-// reference `fu_ref(j)`.  G is KMAX x KMAX and 1 / (G_ii + alpha) KMAX long,
-// zero padded: columns i >= k come out 0 and the loop has no data-dependent
-// branches.  Four FMA chains per column.  Adds the row's F_upd . Y and
-// ||F_upd - F_fix||^2 to the double-float accumulators; returns true when a
-// non-finite value appeared.
-template <int KMAX, class FXA, class FUA>
-__device__ __forceinline__ bool le_hals_row(const float (&y)[KMAX], float alpha, int k, const float4* Gs4,
-                                            const float* inv, FXA fx_at, FUA fu_ref, float2& trv, float2& ddv) {
-  float w[KMAX];
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) w[j] = j < k ? fu_ref(j) : 0.f;
-  // columns in order, each using the columns already updated (G symmetric: row i)
-#pragma unroll
-  for (int i = 0; i < KMAX; ++i) {
-    const float hi = i < k ? fx_at(i) : 0.f;
-    float ac[4] = {fmaf(alpha, hi, y[i]), 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int j4 = 0; j4 < KMAX / 4; ++j4) {
-      const float4 g = Gs4[i * (KMAX / 4) + j4];
-      const float gv[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 4 * j4 + q;
-        if (j != i) ac[q] = fmaf(-w[j], gv[q], ac[q]);
-      }
-    }
-    w[i] = fmaxf(((ac[0] + ac[1]) + (ac[2] + ac[3])) * inv[i], 0.f);
-  }
-  bool bad = false;
-  float t0 = 0.f, t1 = 0.f, d0 = 0.f, d1 = 0.f;
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j)
-    if (j < k) {
-      if (!isfinite(w[j])) bad = true;
-      fu_ref(j) = w[j];
-      const float d = w[j] - fx_at(j);
-      if (j & 1) {
-        t1 = fmaf(w[j], y[j], t1);
-        d1 = fmaf(d, d, d1);
-      } else {
-        t0 = fmaf(w[j], y[j], t0);
-        d0 = fmaf(d, d, d0);
-      }
-    }
-  df_add_f(trv.x, trv.y, t0 + t1);
-  df_add_f(ddv.x, ddv.y, d0 + d1);
-  return bad;
-}
-
 // ------------------------------------------------------------ resident rows
 
 // Column pitch: a multiple of 8 with 32 floats to spare, so that a column
@@ -552,7 +502,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
         float y[KMAX];
 #pragma unroll
         for (int c = 0; c < KMAX; ++c) y[c] = c < k ? Yt[col(c) + r] : 0.f;
-        bad |= le_hals_row<KMAX>(
+        bad |= hals_row_update<KMAX>(
             y, a.alpha, k, Gs4, inv, [&](int i) { return Fx[col(i) + r]; },
             [&](int j) -> float& { return Fu[col(j) + r]; }, trv, ddv);
       }
@@ -710,7 +660,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
               }
             }
           }
-          bad |= le_hals_row<KMAX>(
+          bad |= hals_row_update<KMAX>(
               y, a.alpha, k, Gs4, inv, [&](int i) { return hr[i]; }, [&](int j) -> float& { return wr[j]; }, trv,
               ddv);
         }

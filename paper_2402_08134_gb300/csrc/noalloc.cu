@@ -17,7 +17,8 @@
 namespace {
 
 constexpr int NA_MAX_WIDTH = 64;    // widest F accepted (G is at most 64 x 64)
-constexpr int NA_MAX_BLOCKS = 512;  // block partials the array can hold (2 per SM, up to 256 SMs)
+constexpr int NA_BLOCKS_PER_SM = 2;  // cross-product blocks per SM asked for
+constexpr int NA_MAX_BLOCKS = 512;   // block partials the array can hold (2 per SM, up to 256 SMs)
 constexpr size_t NA_SCRATCH_DOUBLES = (size_t)NA_MAX_BLOCKS * NA_MAX_WIDTH * NA_MAX_WIDTH + 64;
 
 // 16 MiB of block partials plus the kernel's arrival counter (a separate line).
@@ -59,8 +60,8 @@ cudaError_t scratch_for_current_device(DevScratch* out) {
 extern "C" symnmf_status symnmf_gram_noalloc(const float* F, int64_t n, int N, double* G, void* stream) {
   if (!F || !G || n < 1 || N < 1) return SYMNMF_EINVAL;
   if (N > NA_MAX_WIDTH) return SYMNMF_EINVAL;  // beyond the static scratch: at most 64 columns
-  // the cross-product launcher uses at most 2 blocks per SM for widths <= 64
-  if (2 * symnmf::num_sms() > NA_MAX_BLOCKS) return SYMNMF_EUNSUPPORTED;
+  // at most NA_BLOCKS_PER_SM cross-product blocks per SM: their partials fit the array
+  if (NA_BLOCKS_PER_SM * symnmf::num_sms() > NA_MAX_BLOCKS) return SYMNMF_EUNSUPPORTED;
   DevScratch s;
   cudaError_t e = scratch_for_current_device(&s);
   if (e != cudaSuccess) return symnmf::to_status(e);
@@ -69,6 +70,6 @@ extern "C" symnmf_status symnmf_gram_noalloc(const float* F, int64_t n, int N, d
   e = cudaMemsetAsync(s.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return symnmf::to_status(e);
   e = symnmf::xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, s.ws, s.counter,
-                     st);
+                     st, NA_BLOCKS_PER_SM);
   return symnmf::to_status(e);
 }

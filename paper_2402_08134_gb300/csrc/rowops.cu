@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "hals_row.cuh"
 #include "kernels.h"
 
 namespace symnmf {
@@ -213,16 +214,51 @@ cudaError_t xstats(int fmt, const void* x, int64_t ldx, const float* row_scale, 
 constexpr int XC_THREADS = 256;
 constexpr int XC_CHUNK = 128;
 
-size_t xcross_ws_doubles(int la, int lb) { return (size_t)2 * num_sms() * la * lb + 64; }
+// block partials of up to XC_MAX_BLOCKS_PER_SM blocks per SM
+constexpr int XC_MAX_BLOCKS_PER_SM = 4;
+size_t xcross_ws_doubles(int la, int lb) { return (size_t)XC_MAX_BLOCKS_PER_SM * num_sms() * la * lb + 64; }
 
-// C = A^T diag(wt) B over (gathered) rows.  Each thread keeps Kahan-
-// compensated FP32 sums (error O(eps) however many rows they cover); row
-// groups and block partials combine as double-float pairs (dfloat.cuh): no
-// FP64 arithmetic, which is scarce on this part.  The trace-trick objective
-// cancels terms of size ||X||^2, so the Grams need this accuracy.  Block
-// partials are summed in block order (deterministic), by the last block or by
-// a second kernel.
-template <int TPT>
+// C = A^T diag(wt) B over (gathered) rows.  Each thread owns 4 x 4 tiles of
+// C.  It sums up to XC_SUB of its rows with plain FMAs, then adds that sum to
+// a Kahan-compensated FP32 total, so the error stays at a few XC_SUB ulps
+// however many rows the thread covers, at one FMA per product.  Row groups
+// and block partials combine as double-float pairs (dfloat.cuh): no FP64
+// arithmetic, which is scarce on this part.  The trace-trick objective cancels
+// terms of size ||X||^2, so the Grams need this accuracy.  Block partials are
+// summed in block order (deterministic), by the last block or by a second
+// kernel.  VEC: 16-byte loads of whole rows (la, lb, lda, ldb multiples of 4,
+// aligned operands).
+constexpr int XC_SUB = 32;
+
+// Tile index -> (row tile, column tile): row-major over all ta x tb tiles, or
+// over the upper triangle (ti <= tj) of a symmetric product.
+__device__ __forceinline__ void xc_tile(int tile, bool sym, int ta, int tb, int& ti, int& tj) {
+  if (!sym) {
+    ti = tile / tb;
+    tj = tile - ti * tb;
+    return;
+  }
+  ti = 0;
+  while (tile >= ta - ti) {
+    tile -= ta - ti;
+    ++ti;
+  }
+  tj = ti + tile;
+}
+
+// Entry (i, j) of a block partial; a symmetric product keeps i <= j and
+// writes it to both positions.
+__device__ __forceinline__ void xc_emit(dfl* out, int la, int lb, bool sym, int i, int j, dfl v) {
+  if (i >= la || j >= lb) return;
+  if (!sym) {
+    out[i * lb + j] = v;
+  } else if (i <= j) {
+    out[i * lb + j] = v;
+    out[j * lb + i] = v;
+  }
+}
+
+template <int TPT, bool VEC>
 __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
     const float* __restrict__ A, int lda, int la, const float* __restrict__ B, int ldb, int lb,
     int64_t n, const int32_t* __restrict__ idx, const float* __restrict__ wt, const int* cnt,
@@ -231,13 +267,18 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   extern __shared__ __align__(16) unsigned char smraw[];
   const int la4 = (la + 3) & ~3, lb4 = (lb + 3) & ~3;
   float* As = (float*)smraw;
+  // a Gram (same operand, no weights) stages its rows once
+  const bool same = (A == B) && (lda == ldb) && (la == lb) && !wt;
   float* Bs = As + XC_CHUNK * la4;
-  dfl* red = (dfl*)(Bs + XC_CHUNK * lb4);
+  dfl* red = (dfl*)(Bs + (same ? 0 : XC_CHUNK * lb4));
   dfl* wsd = reinterpret_cast<dfl*>(ws);  // the partials are double-float pairs
-  const int ta = la4 >> 2, tb = lb4 >> 2, T = ta * tb;
-  const int tid = threadIdx.x;
-  const int R = T >= XC_THREADS ? 1 : XC_THREADS / T;
-  const int rg = T >= XC_THREADS ? 0 : tid / T;
+  // a symmetric product (same operand on both sides, weights allowed) covers
+  // the upper tiles only and mirrors them: exactly symmetric, half the work
+  const bool sym = (A == B) && (lda == ldb) && (la == lb);
+  const int ta = la4 >> 2, tb = lb4 >> 2, T = sym ? ta * (ta + 1) / 2 : ta * tb;
+  const int tid = threadIdx.x, nt = blockDim.x;  // nt = XC_THREADS when T > nt
+  const int R = T >= nt ? 1 : nt / T;
+  const int rg = T >= nt ? 0 : tid / T;
   const bool active = rg < R;
 
   const int64_t count = cnt ? (int64_t)(*cnt) : n;
@@ -251,63 +292,90 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
 #pragma unroll
     for (int e = 0; e < 16; ++e) f[t][e] = 0.f, fc[t][e] = 0.f;
 
-  // a Gram (same operand, no weights) stages its rows once
-  const bool same = (A == B) && (lda == ldb) && (la == lb) && !wt;
   const float* Bsrc = same ? As : Bs;
-  // pad columns are zero once and for all
-  if (la4 > la)
-    for (int e = tid; e < XC_CHUNK * (la4 - la); e += XC_THREADS) As[(e / (la4 - la)) * la4 + la + e % (la4 - la)] = 0.f;
-  if (!same && lb4 > lb)
-    for (int e = tid; e < XC_CHUNK * (lb4 - lb); e += XC_THREADS) Bs[(e / (lb4 - lb)) * lb4 + lb + e % (lb4 - lb)] = 0.f;
+  // staging map: each thread copies one 4-column group of rows my_r, my_r + rpp, ...
+  const int a_r = tid / ta, a_c = tid - a_r * ta, a_rpp = nt / ta;
+  const int b_r = tid / tb, b_c = tid - b_r * tb, b_rpp = nt / tb;
+  // each thread's tiles
+  int tile_i[TPT], tile_j[TPT];
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    const int tile = (T >= nt) ? tid + t * nt : tid % T;
+    xc_tile(tile < T ? tile : 0, sym, ta, tb, tile_i[t], tile_j[t]);
+    if (tile >= T || !active) tile_i[t] = -1;  // idle threads own no tile
+  }
   for (int64_t rb = r0; rb < r1; rb += XC_CHUNK) {
-    // stage the chunk: flattened over (row, column) so that every thread's
-    // loads are independent of one another (many in flight); rows past the
-    // end are zero
+    // stage the chunk (rows past the end and pad columns are zero)
     const int rows = (int)min((int64_t)XC_CHUNK, r1 - rb);
+    if (a_r < a_rpp) {
 #pragma unroll 4
-    for (int e = tid; e < XC_CHUNK * la; e += XC_THREADS) {
-      const int rr = e / la, c = e - rr * la;
-      float v = 0.f;
-      if (rr < rows) {
-        const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
-        v = A[src * lda + c];
-      }
-      As[rr * la4 + c] = v;
-    }
-    if (!same) {
-#pragma unroll 4
-      for (int e = tid; e < XC_CHUNK * lb; e += XC_THREADS) {
-        const int rr = e / lb, c = e - rr * lb;
-        float v = 0.f;
+      for (int rr = a_r; rr < XC_CHUNK; rr += a_rpp) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (rr < rows) {
           const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
-          v = B[src * ldb + c] * (wt ? __ldg(wt + rb + rr) : 1.f);
+          const float* ar = A + src * lda + 4 * a_c;
+          if constexpr (VEC) {
+            v = __ldg(reinterpret_cast<const float4*>(ar));
+          } else {
+            const int c = 4 * a_c;
+            v.x = __ldg(ar);
+            if (c + 1 < la) v.y = __ldg(ar + 1);
+            if (c + 2 < la) v.z = __ldg(ar + 2);
+            if (c + 3 < la) v.w = __ldg(ar + 3);
+          }
         }
-        Bs[rr * lb4 + c] = v;
+        *reinterpret_cast<float4*>(As + rr * la4 + 4 * a_c) = v;
+      }
+    }
+    if (!same && b_r < b_rpp) {
+#pragma unroll 4
+      for (int rr = b_r; rr < XC_CHUNK; rr += b_rpp) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rr < rows) {
+          const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
+          const float* br = B + src * ldb + 4 * b_c;
+          if constexpr (VEC) {
+            v = __ldg(reinterpret_cast<const float4*>(br));
+          } else {
+            const int c = 4 * b_c;
+            v.x = __ldg(br);
+            if (c + 1 < lb) v.y = __ldg(br + 1);
+            if (c + 2 < lb) v.z = __ldg(br + 2);
+            if (c + 3 < lb) v.w = __ldg(br + 3);
+          }
+          if (wt) {
+            const float w = __ldg(wt + rb + rr);
+            v.x *= w, v.y *= w, v.z *= w, v.w *= w;
+          }
+        }
+        *reinterpret_cast<float4*>(Bs + rr * lb4 + 4 * b_c) = v;
       }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int t = 0; t < TPT; ++t) {
-        const int tile = (T >= XC_THREADS) ? tid + t * XC_THREADS : tid % T;
-        if (tile < T) {
-          const int ti = tile / tb, tj = tile - ti * tb;
-          for (int rr = rg; rr < rows; rr += R) {
-            const float4 a = *(const float4*)(As + rr * la4 + 4 * ti);
-            const float4 b = *(const float4*)(Bsrc + rr * lb4 + 4 * tj);
-            const float av[4] = {a.x, a.y, a.z, a.w};
-            const float bv[4] = {b.x, b.y, b.z, b.w};
+        if (tile_i[t] >= 0) {
+          const float* ap = As + 4 * tile_i[t];
+          const float* bp = Bsrc + 4 * tile_j[t];
+          for (int s0 = rg; s0 < rows; s0 += XC_SUB * R) {
+            const int s1 = min(rows, s0 + XC_SUB * R);
+            float p[16];
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+            for (int e = 0; e < 16; ++e) p[e] = 0.f;
+#pragma unroll 4
+            for (int rr = s0; rr < s1; rr += R) {
+              const float4 a = *reinterpret_cast<const float4*>(ap + rr * la4);
+              const float4 b = *reinterpret_cast<const float4*>(bp + rr * lb4);
+              const float av[4] = {a.x, a.y, a.z, a.w};
+              const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                // Kahan step: y = a b - c; t = s + y; c = (t - s) - y; s = t
-                const float y = fmaf(av[p], bv[q], -fc[t][p * 4 + q]);
-                const float s2 = f[t][p * 4 + q] + y;
-                fc[t][p * 4 + q] = (s2 - f[t][p * 4 + q]) - y;
-                f[t][p * 4 + q] = s2;
-              }
+              for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) p[pp * 4 + q] = fmaf(av[pp], bv[q], p[pp * 4 + q]);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) kahan_add(f[t][e], fc[t][e], p[e]);
           }
         }
       }
@@ -329,28 +397,25 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
       }
       __syncthreads();
     }
-    for (int e = tid; e < T * 16; e += XC_THREADS) {
-      const int tile = e >> 4, w = e & 15;
-      const int i = (tile / tb) * 4 + (w >> 2), j = (tile % tb) * 4 + (w & 3);
-      if (i < la && j < lb) wsd[(size_t)blockIdx.x * LL + i * lb + j] = red[e];
+    for (int e = tid; e < T * 16; e += nt) {
+      int ti, tj;
+      xc_tile(e >> 4, sym, ta, tb, ti, tj);
+      xc_emit(wsd + (size_t)blockIdx.x * LL, la, lb, sym, ti * 4 + ((e & 15) >> 2), tj * 4 + (e & 3), red[e]);
     }
   } else {
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-      const int tile = tid + t * XC_THREADS;
-      if (tile < T) {
-        const int ti = tile / tb, tj = tile - ti * tb;
+      if (tile_i[t] >= 0) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int i = ti * 4 + (e >> 2), j = tj * 4 + (e & 3);
-          if (i < la && j < lb) wsd[(size_t)blockIdx.x * LL + i * lb + j] = dfl{f[t][e], -fc[t][e]};
-        }
+        for (int e = 0; e < 16; ++e)
+          xc_emit(wsd + (size_t)blockIdx.x * LL, la, lb, sym, tile_i[t] * 4 + (e >> 2), tile_j[t] * 4 + (e & 3),
+                  dfl{f[t][e], -fc[t][e]});
       }
     }
   }
   if (counter && last_block<1>(counter)) {
     const unsigned G = gridDim.x;
-    for (int e = tid; e < LL; e += XC_THREADS) {
+    for (int e = tid; e < LL; e += nt) {
       // four independent chains keep several L2 loads in flight (fixed order)
       dfl s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
       unsigned b = 0;
@@ -410,36 +475,40 @@ __global__ void xcross_reduce_kernel(const double* __restrict__ ws, int G, int L
 cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int lb, int64_t n,
                    const int32_t* idx, const float* wt, const int* cnt, const double* lam,
                    double shift, double* C, float* Cf, double* ws, unsigned* counter,
-                   cudaStream_t st) {
+                   cudaStream_t st, int max_blocks_per_sm) {
   if (la < 1 || lb < 1 || la > 128 || lb > 128) return cudaErrorInvalidValue;
+  if (max_blocks_per_sm < 1 || max_blocks_per_sm > XC_MAX_BLOCKS_PER_SM) return cudaErrorInvalidValue;
   const int la4 = (la + 3) & ~3, lb4 = (lb + 3) & ~3;
-  const int T = (la4 / 4) * (lb4 / 4);
-  const size_t smem = (size_t)XC_CHUNK * (la4 + lb4) * 4 + (size_t)(T < XC_THREADS ? T : 0) * 16 * 8;
-  int grid = (int)((n + 255) / 256);
-  const int cap = num_sms() * ((size_t)la * lb <= 4096 ? 2 : 1);
-  if (grid > cap) grid = cap;
+  const bool sym = (A == B) && (lda == ldb) && (la == lb);
+  const bool same = sym && !wt;
+  const int T = sym ? (la4 / 4) * (la4 / 4 + 1) / 2 : (la4 / 4) * (lb4 / 4);
+  // as many threads as tiles x row groups use (whole warps): narrow products
+  // leave room for more blocks per SM
+  const int nthreads = T >= XC_THREADS ? XC_THREADS : ((XC_THREADS / T) * T + 31) / 32 * 32;
+  const size_t smem =
+      (size_t)XC_CHUNK * (la4 + (same ? 0 : lb4)) * 4 + (size_t)(T < XC_THREADS ? T : 0) * 16 * 8;
+  const int tpt = T <= XC_THREADS ? 1 : T <= 2 * XC_THREADS ? 2 : 4;
+  const bool vec = (la % 4) == 0 && (lb % 4) == 0 && (lda % 4) == 0 && (ldb % 4) == 0 &&
+                   (((uintptr_t)A | (uintptr_t)B) & 15) == 0;
+  const void* fn = tpt == 1 ? (vec ? (const void*)xcross_kernel<1, true> : (const void*)xcross_kernel<1, false>)
+                   : tpt == 2 ? (vec ? (const void*)xcross_kernel<2, true> : (const void*)xcross_kernel<2, false>)
+                              : (vec ? (const void*)xcross_kernel<4, true> : (const void*)xcross_kernel<4, false>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nthreads, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, std::min(per_sm, max_blocks_per_sm));
+  int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * per_sm);
   if (grid < 1) grid = 1;
   // many partials of many entries: reduce them with the whole GPU instead of one block
   const int LL = la * lb;
   const bool two_stage = grid >= 16 && (int64_t)grid * LL > 16384;
   unsigned* ctr = two_stage ? nullptr : counter;
-  cudaError_t e;
-  if (T <= XC_THREADS) {
-    e = cudaFuncSetAttribute(xcross_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    xcross_kernel<1><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, ctr);
-  } else if (T <= 2 * XC_THREADS) {
-    e = cudaFuncSetAttribute(xcross_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    xcross_kernel<2><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, ctr);
-  } else {
-    e = cudaFuncSetAttribute(xcross_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    xcross_kernel<4><<<grid, XC_THREADS, smem, st>>>(A, lda, la, B, ldb, lb, n, idx, wt, cnt, lam,
-                                                     shift, C, Cf, ws, ctr);
-  }
+  void* args[] = {(void*)&A, (void*)&lda, (void*)&la, (void*)&B,   (void*)&ldb, (void*)&lb, (void*)&n,   (void*)&idx,
+                  (void*)&wt, (void*)&cnt, (void*)&lam, (void*)&shift, (void*)&C,   (void*)&Cf, (void*)&ws, (void*)&ctr};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(nthreads), args, smem, st);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   if (two_stage) {
     const int warps_per_block = 8;
@@ -452,141 +521,120 @@ cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int
 
 // ------------------------------------------------------------------ HALS
 
-constexpr int HALS_ROWS = 64;  // rows per tile = threads per block
+constexpr int HALS_THREADS = 128;
 
-// One thread per row.  Per group g (k columns, its own Gram G_g):
-//   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
-// i = 0..k-1 in order with the columns already updated (Eq. symhals_update2).
+// Threads per row of the full-X HALS kernel.  A split over a lane pair (half
+// the registers, twice the warps) measured slower at k = 64 (766 vs 664 us at
+// n = 10^6): the shuffle joins every column's dependency chain, which is bound
+// by shared-memory load latency already.
 template <int KMAX>
-__global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
-    float* __restrict__ Fu, const float* __restrict__ Ff, int64_t n, int k, int ng,
-    const float* __restrict__ G, float alpha, const float* __restrict__ Y, int ldy,
-    const float* __restrict__ U, int l, const float* __restrict__ M, double* part, double* ws,
-    unsigned* counter, unsigned* err) {
+constexpr int hals_ns() {
+  return 1;
+}
+
+// Full-X HALS update, Eq. symhals_update2:
+//   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
+// i = 0..k-1 in order with the columns already updated.  NS = hals_ns threads
+// per row, each holding its KMAX / NS columns of F_upd and of Y in registers
+// (zero padded; 16-byte loads when VEC); G with its diagonal zeroed and the
+// reciprocals 1 / (G_ii + alpha) in shared memory, read as broadcasts.  With U
+// given the row of Y is formed in registers as U_r M (LAI, M = Lambda U^T F_fix
+// in shared memory).  Persistent grid over rows; F_upd . Y and
+// ||F_upd - F_fix||^2 are kept per thread in double-float and reduced in FP64.
+template <int KMAX, bool VEC>
+__global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
+    float* __restrict__ Fu, const float* __restrict__ Ff, int64_t n, int k, const float* __restrict__ G, float alpha,
+    const float* __restrict__ Y, int ldy, const float* __restrict__ U, int l, const float* __restrict__ M,
+    double* part, double* ws, unsigned* counter, unsigned* err) {
+  constexpr int NS = hals_ns<KMAX>(), KH = KMAX / NS;
+  constexpr int RS = hals_split_stride<KMAX, NS>();
+  constexpr int RPB = HALS_THREADS / NS;  // rows per block and pass
   extern __shared__ __align__(16) float sm[];
-  const int RW = ng * k;         // row width
-  const int P = RW + 1;          // odd smem row pitch: conflict-free per-row reads
-  const int k4 = (k + 3) & ~3, k4q = k4 / 4;
-  float* Gs = sm;                  // ng x k x k4, zero padded (G symmetric: row i = column i)
-  float* inv = Gs + ng * k * k4;   // ng x k4
-  float* Ms = inv + ng * k4;       // l x k4 (LAI only, ng == 1), zero padded
-  float* Ys = Ms + (U ? l * k4 : 0);  // HALS_ROWS x P
-  float* Hs = Ys + HALS_ROWS * P;
-  float* Ws = Hs + HALS_ROWS * P;
-  float* Us = Ws + HALS_ROWS * P;  // HALS_ROWS x (l + 1) (LAI only)
+  float* Gs = sm;               // KMAX x RS, diagonal zeroed
+  float* inv = Gs + KMAX * RS;  // KMAX
+  float* Ms = inv + KMAX;       // l x KMAX (LAI only)
   const int tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  for (int e = tid; e < ng * k * k4; e += HALS_ROWS) {
-    const int gi = e / k4, j = e - gi * k4;  // gi = g * k + i
-    Gs[e] = j < k ? G[gi * k + j] : 0.f;
+  for (int e = tid; e < KMAX * KMAX; e += HALS_THREADS) {
+    const int i = e / KMAX, j = e - i * KMAX;
+    const int part = j / KH;
+    Gs[i * RS + part * (NS > 1 ? KH + 4 : KH) + (j - part * KH)] = (i < k && j < k && i != j) ? G[i * k + j] : 0.f;
   }
   if (U)
-    for (int e = tid; e < l * k4; e += HALS_ROWS) {
-      const int i = e / k4, j = e - i * k4;
+    for (int e = tid; e < l * KMAX; e += HALS_THREADS) {
+      const int i = e / KMAX, j = e - i * KMAX;
       Ms[e] = j < k ? M[i * k + j] : 0.f;
     }
+  if (tid < KMAX) inv[tid] = tid < k ? 1.0f / (G[tid * k + tid] + alpha) : 0.f;
   __syncthreads();
-  for (int e = tid; e < ng * k4; e += HALS_ROWS) {
-    const int g = e / k4, i = e - g * k4;
-    inv[e] = i < k ? 1.0f / (Gs[(g * k + i) * k4 + i] + alpha) : 0.f;
-  }
-  __syncthreads();
-  const float4* Gs4 = reinterpret_cast<const float4*>(Gs);
-  const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
 
-  double tr = 0.0, dd = 0.0;
+  const int p = NS > 1 ? (tid & 1) : 0;            // this thread's part of its row
+  const unsigned mask = NS > 1 ? 3u << (tid & 30) : 0xffffffffu;
+  const int c0 = p * KH;                             // its first column
+  const float4* Gp4 = reinterpret_cast<const float4*>(Gs + p * (KH + 4));
+  const float4* Ms4 = reinterpret_cast<const float4*>(Ms + c0);
+  float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
   bool bad = false;
-  const int64_t ntiles = (n + HALS_ROWS - 1) / HALS_ROWS;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t base = tile * HALS_ROWS;
-    const int rows = (int)min((int64_t)HALS_ROWS, n - base);
-    // coalesced staging, one warp per row (no index division)
-    for (int rr = wid; rr < rows; rr += HALS_ROWS / 32) {
-      const int64_t g = (base + rr);
-      for (int c = lane; c < RW; c += 32) {
-        Hs[rr * P + c] = Ff[g * RW + c];
-        Ws[rr * P + c] = Fu[g * RW + c];
-        if (!U) Ys[rr * P + c] = Y[g * (int64_t)ldy + c];
+  for (int64_t r = (int64_t)blockIdx.x * RPB + tid / NS; r < n; r += (int64_t)gridDim.x * RPB) {
+    float y[KH], w[KH];
+    float* fu = Fu + r * k + c0;
+    const float* fx = Ff + r * k + c0;
+    if constexpr (VEC) {
+#pragma unroll
+      for (int q = 0; q < KH / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + 4 * q < k) v = __ldg(reinterpret_cast<const float4*>(fu) + q);
+        w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
       }
-      if (U)
-        for (int c = lane; c < l; c += 32) Us[rr * (l + 1) + c] = U[g * (int64_t)l + c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < KH; ++c) w[c] = c0 + c < k ? __ldg(fu + c) : 0.f;
     }
-    __syncthreads();
-    if (tid < rows) {
-      const float* yr = Ys + tid * P;
-      const float* hr = Hs + tid * P;
-      float* wr = Ws + tid * P;
-      for (int g = 0; g < ng; ++g) {
-        const int o = g * k;
-        const float4* Gg4 = Gs4 + (size_t)g * k * k4q;
-        float y[KMAX];
-        if (U) {  // Y_r = U_r M (LAI product fused into the update), in registers
-          const float* ur = Us + tid * (l + 1);
+    if (U) {  // Y_r = U_r M (LAI product fused into the update)
 #pragma unroll
-          for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
-          for (int p = 0; p < l; ++p) {
-            const float u = ur[p];
+      for (int c = 0; c < KH; ++c) y[c] = 0.f;
+      const float* ur = U + r * l;
+#pragma unroll 2
+      for (int pp = 0; pp < l; ++pp) {
+        const float u = __ldg(ur + pp);
 #pragma unroll
-            for (int c4 = 0; c4 < KMAX / 4; ++c4)
-              if (c4 < k4q) {
-                const float4 m = Ms4[p * k4q + c4];
-                y[4 * c4 + 0] = fmaf(u, m.x, y[4 * c4 + 0]);
-                y[4 * c4 + 1] = fmaf(u, m.y, y[4 * c4 + 1]);
-                y[4 * c4 + 2] = fmaf(u, m.z, y[4 * c4 + 2]);
-                y[4 * c4 + 3] = fmaf(u, m.w, y[4 * c4 + 3]);
-              }
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < KMAX; ++c) y[c] = c < k ? yr[o + c] : 0.f;
+        for (int q = 0; q < KH / 4; ++q) {
+          const float4 m = Ms4[pp * (KMAX / 4) + q];
+          y[4 * q + 0] = fmaf(u, m.x, y[4 * q + 0]);
+          y[4 * q + 1] = fmaf(u, m.y, y[4 * q + 1]);
+          y[4 * q + 2] = fmaf(u, m.z, y[4 * q + 2]);
+          y[4 * q + 3] = fmaf(u, m.w, y[4 * q + 3]);
         }
-        float w[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) w[j] = j < k ? wr[o + j] : 0.f;
-#pragma unroll
-        for (int i = 0; i < KMAX; ++i) {
-          if (i < k) {
-            // two independent chains halve the FMA latency of the column update
-            float a0 = fmaf(alpha, hr[o + i], y[i]), a1 = 0.f;
-#pragma unroll
-            for (int j4 = 0; j4 < KMAX / 4; ++j4)
-              if (j4 < k4q) {
-                const float4 gq = Gg4[i * k4q + j4];
-                const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const int j = 4 * j4 + u;
-                  if (j != i) {  // zero pads: j >= k adds nothing
-                    if (u & 1)
-                      a1 = fmaf(-w[j], gv[u], a1);
-                    else
-                      a0 = fmaf(-w[j], gv[u], a0);
-                  }
-                }
-              }
-            w[i] = fmaxf((a0 + a1) * inv[g * k4 + i], 0.f);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-          if (j < k) {
-            if (!isfinite(w[j])) bad = true;
-            wr[o + j] = w[j];
-            tr += (double)w[j] * (double)y[j];
-            const float d = w[j] - hr[o + j];
-            dd += (double)d * (double)d;
-          }
       }
+    } else if constexpr (VEC) {
+      const float* yr = Y + r * ldy + c0;
+#pragma unroll
+      for (int q = 0; q < KH / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + 4 * q < k) v = __ldg(reinterpret_cast<const float4*>(yr) + q);
+        y[4 * q] = v.x, y[4 * q + 1] = v.y, y[4 * q + 2] = v.z, y[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < KH; ++c) y[c] = c0 + c < k ? __ldg(Y + r * ldy + c0 + c) : 0.f;
     }
-    __syncthreads();
-    for (int rr = tid >> 5; rr < rows; rr += HALS_ROWS / 32)
-      for (int c = tid & 31; c < RW; c += 32) Fu[(base + rr) * RW + c] = Ws[rr * P + c];
-    __syncthreads();
+    // the fixed row is read column by column (L1 hits after the first)
+    bad |= hals_row_split<KMAX, NS>(w, y, alpha, k, p, mask, Gp4, inv, [&](int c) { return __ldg(fx + c); }, trv,
+                                    ddv);
+    if constexpr (VEC) {
+#pragma unroll
+      for (int q = 0; q < KH / 4; ++q)
+        if (c0 + 4 * q < k)
+          reinterpret_cast<float4*>(fu)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < KH; ++c)
+        if (c0 + c < k) fu[c] = w[c];
+    }
   }
   if (bad) set_error(err, ERR_NAN);
   __shared__ double sh[32];
-  tr = block_sum(tr, sh);
-  dd = block_sum(dd, sh);
+  const double tr = block_sum((double)trv.x + (double)trv.y, sh);
+  const double dd = block_sum((double)ddv.x + (double)ddv.y, sh);
   if (tid == 0) {
     ws[2 * blockIdx.x] = tr;
     ws[2 * blockIdx.x + 1] = dd;
@@ -597,39 +645,51 @@ __global__ void __launch_bounds__(HALS_ROWS) hals_kernel(
   }
 }
 
-template <int KMAX>
-static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, int ng, const float* G,
-                               double alpha, const float* Y, int ldy, const float* U, int l,
-                               const float* M, double* part, double* ws, unsigned* counter,
-                               unsigned* err, cudaStream_t st) {
-  if (U && ng != 1) return cudaErrorInvalidValue;
-  const int RW = ng * k, P = RW + 1, k4 = (k + 3) & ~3;
-  size_t smem = (size_t)(ng * k * k4 + ng * k4 + 3 * HALS_ROWS * P) * 4;
-  if (U) smem += (size_t)(HALS_ROWS * (l + 1) + l * k4) * 4;
-  cudaError_t e = cudaFuncSetAttribute(hals_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+template <int KMAX, bool VEC>
+static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, const float* G, double alpha,
+                               const float* Y, int ldy, const float* U, int l, const float* M, double* part,
+                               double* ws, unsigned* counter, unsigned* err, cudaStream_t st) {
+  size_t smem = (size_t)(KMAX * hals_split_stride<KMAX, hals_ns<KMAX>()>() + KMAX) * 4;
+  if (U) smem += (size_t)l * KMAX * 4;
+  auto kern = hals_kernel<KMAX, VEC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (n + HALS_ROWS - 1) / HALS_ROWS;
-  int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 4);
-  if (grid < 1) grid = 1;
-  hals_kernel<KMAX><<<grid, HALS_ROWS, smem, st>>>(Fu, Ff, n, k, ng, G, (float)alpha, Y, ldy, U, l, M,
-                                                   part, ws, counter, err);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HALS_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t rpb = HALS_THREADS / hals_ns<KMAX>();
+  const int64_t tiles = (n + rpb - 1) / rpb;
+  // at most 2048 blocks: one FP64 partial pair per block in ws
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * std::min(std::max(per_sm, 1), 8));
+  grid = std::max(1, std::min(grid, 2048));
+  kern<<<grid, HALS_THREADS, smem, st>>>(Fu, Ff, n, k, G, (float)alpha, Y, ldy, U, l, M, part, ws, counter, err);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t hals_update(float* F_upd, const float* F_fix, int64_t n, int k, int ngroups,
-                        const float* G, double alpha, const float* Y, int ldy, const float* U, int l,
-                        const float* M, double* part, double* ws, unsigned* counter, unsigned* err,
-                        cudaStream_t st) {
-  if (k <= 8)
-    return launch_hals<8>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
-  if (k <= 16)
-    return launch_hals<16>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
-  if (k <= 32)
-    return launch_hals<32>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
-  if (k <= 64)
-    return launch_hals<64>(F_upd, F_fix, n, k, ngroups, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+template <int KMAX>
+static cudaError_t launch_hals_v(float* Fu, const float* Ff, int64_t n, int k, const float* G, double alpha,
+                                 const float* Y, int ldy, const float* U, int l, const float* M, double* part,
+                                 double* ws, unsigned* counter, unsigned* err, cudaStream_t st) {
+  const bool vec = (k % 4) == 0 && (ldy % 4) == 0 &&
+                   (((uintptr_t)Fu | (uintptr_t)Ff | (uintptr_t)(Y ? Y : Fu)) & 15) == 0;
+  return vec ? launch_hals<KMAX, true>(Fu, Ff, n, k, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st)
+             : launch_hals<KMAX, false>(Fu, Ff, n, k, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st);
+}
+
+cudaError_t hals_update(float* F_upd, const float* F_fix, int64_t n, int k, const float* G, double alpha,
+                        const float* Y, int ldy, const float* U, int l, const float* M, double* part, double* ws,
+                        unsigned* counter, unsigned* err, cudaStream_t st) {
+  if (k < 1 || n < 0) return cudaErrorInvalidValue;
+#define SYMNMF_HALS(KM) \
+  return launch_hals_v<KM>(F_upd, F_fix, n, k, G, alpha, Y, ldy, U, l, M, part, ws, counter, err, st)
+  if (k <= 8) SYMNMF_HALS(8);
+  if (k <= 16) SYMNMF_HALS(16);
+  if (k <= 24) SYMNMF_HALS(24);
+  if (k <= 32) SYMNMF_HALS(32);
+  if (k <= 48) SYMNMF_HALS(48);
+  if (k <= 64) SYMNMF_HALS(64);
+#undef SYMNMF_HALS
   return cudaErrorInvalidValue;
 }
 
@@ -676,58 +736,86 @@ cudaError_t apply_small(const float* A, int lda, int la, const float* B, int lb,
 
 // ------------------------------------------------------------- leverage
 
-constexpr int LEV_ROWS = 128;
+constexpr int LEV_THREADS = 128;
 
-// One thread per row; the block's rows are staged through shared memory with
-// coalesced loads (row pitch k + 1 avoids bank conflicts).
-template <int KMAX>
-__global__ void __launch_bounds__(LEV_ROWS) leverage_kernel(const float* __restrict__ F, int64_t n, int k,
-                                                            const float* __restrict__ Rinv, double* lev) {
-  __shared__ float Rs[KMAX * KMAX];
-  __shared__ float Fs[LEV_ROWS * (KMAX + 1)];
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rs[e] = Rinv[e];
-  const int64_t base = (int64_t)blockIdx.x * LEV_ROWS;
-  const int rows = (int)min((int64_t)LEV_ROWS, n - base);
-  for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
-    const int rr = e / k, c = e - rr * k;
-    Fs[rr * (k + 1) + c] = F[base * k + e];
+// l_i = ||h_i R^-1||^2 (R^-1 upper triangular, Alg. LvS-SymNMF).  One thread
+// per row: z = h R^-1 accumulated by rows of R^-1 (z_j += h_p R^-1_pj for
+// j >= p), read as float4 broadcasts from shared memory (KMAX x KMAX, zero
+// padded), so every load feeds four FMAs; the row of F in registers, read with
+// 16-byte loads when VEC.
+template <int KMAX, bool VEC>
+__global__ void __launch_bounds__(LEV_THREADS) leverage_kernel(const float* __restrict__ F, int64_t n, int k,
+                                                               const float* __restrict__ Rinv, double* lev) {
+  __shared__ __align__(16) float Rs[KMAX * KMAX];
+  for (int e = threadIdx.x; e < KMAX * KMAX; e += LEV_THREADS) {
+    const int p = e / KMAX, j = e - p * KMAX;
+    Rs[e] = (p < k && j < k && p <= j) ? Rinv[p * k + j] : 0.f;
   }
   __syncthreads();
-  if ((int)threadIdx.x >= rows) return;
-  float h[KMAX];
+  const float4* R4 = reinterpret_cast<const float4*>(Rs);
+  for (int64_t r = (int64_t)blockIdx.x * LEV_THREADS + threadIdx.x; r < n; r += (int64_t)gridDim.x * LEV_THREADS) {
+    const float* fr = F + r * k;
+    float h[KMAX];
+    if constexpr (VEC) {
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j) h[j] = j < k ? Fs[threadIdx.x * (k + 1) + j] : 0.f;
-  float s = 0.f;
-  // z_j = sum_{p <= j} h_p Rinv[p][j]  (Rinv upper triangular)
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    if (j < k) {
-      float z0 = 0.f, z1 = 0.f;
-#pragma unroll
-      for (int p = 0; p <= j; ++p) {
-        if (p & 1)
-          z1 = fmaf(h[p], Rs[p * k + j], z1);
-        else
-          z0 = fmaf(h[p], Rs[p * k + j], z0);
+      for (int q = 0; q < KMAX / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * q < k) v = __ldg(reinterpret_cast<const float4*>(fr) + q);
+        h[4 * q] = v.x, h[4 * q + 1] = v.y, h[4 * q + 2] = v.z, h[4 * q + 3] = v.w;
       }
-      const float z = z0 + z1;
-      s = fmaf(z, z, s);
+    } else {
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c) h[c] = c < k ? __ldg(fr + c) : 0.f;
     }
+    float z[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) z[j] = 0.f;
+#pragma unroll
+    for (int p = 0; p < KMAX; ++p)
+#pragma unroll
+      for (int j4 = p / 4; j4 < KMAX / 4; ++j4) {
+        const float4 g = R4[p * (KMAX / 4) + j4];
+        z[4 * j4 + 0] = fmaf(h[p], g.x, z[4 * j4 + 0]);
+        z[4 * j4 + 1] = fmaf(h[p], g.y, z[4 * j4 + 1]);
+        z[4 * j4 + 2] = fmaf(h[p], g.z, z[4 * j4 + 2]);
+        z[4 * j4 + 3] = fmaf(h[p], g.w, z[4 * j4 + 3]);
+      }
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < KMAX; j += 2) {
+      s0 = fmaf(z[j], z[j], s0);
+      s1 = fmaf(z[j + 1], z[j + 1], s1);
+    }
+    lev[r] = (double)(s0 + s1);
   }
-  lev[base + threadIdx.x] = (double)s;
+}
+
+template <int KMAX>
+static void launch_leverage(const float* F, int64_t n, int k, const float* Rinv, double* lev, cudaStream_t st) {
+  const int64_t blocks = (n + LEV_THREADS - 1) / LEV_THREADS;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 8));
+  if ((k % 4) == 0 && ((uintptr_t)F & 15) == 0)
+    leverage_kernel<KMAX, true><<<grid, LEV_THREADS, 0, st>>>(F, n, k, Rinv, lev);
+  else
+    leverage_kernel<KMAX, false><<<grid, LEV_THREADS, 0, st>>>(F, n, k, Rinv, lev);
 }
 
 cudaError_t leverage_rows(const float* F, int64_t n, int k, const float* Rinv, double* lev,
                           cudaStream_t st) {
-  const int grid = (int)((n + LEV_ROWS - 1) / LEV_ROWS);
-  if (k <= 16)
-    leverage_kernel<16><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  if (n < 1) return cudaSuccess;
+  if (k <= 8)
+    launch_leverage<8>(F, n, k, Rinv, lev, st);
+  else if (k <= 16)
+    launch_leverage<16>(F, n, k, Rinv, lev, st);
+  else if (k <= 24)
+    launch_leverage<24>(F, n, k, Rinv, lev, st);
   else if (k <= 32)
-    leverage_kernel<32><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
-  else if (k <= 64)
-    leverage_kernel<64><<<grid, LEV_ROWS, 0, st>>>(F, n, k, Rinv, lev);
+    launch_leverage<32>(F, n, k, Rinv, lev, st);
+  else if (k <= 48)
+    launch_leverage<48>(F, n, k, Rinv, lev, st);
   else
-    return cudaErrorInvalidValue;
+    launch_leverage<64>(F, n, k, Rinv, lev, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -870,13 +958,17 @@ cudaError_t philox_gaussian(float* out, int64_t n, int l, uint64_t seed, cudaStr
 // scale_mul * sqrt(scale_num[0]) when scale_num != NULL, else 1.
 __global__ void uniform_kernel(float* out, int64_t n, int k, uint32_t k0, uint32_t k1,
                                const double* scale_num, double scale_mul) {
+  // the scale once per block: FP64 square roots are scarce on this part
+  __shared__ double scale;
+  if (threadIdx.x == 0) scale = scale_num ? scale_mul * sqrt(scale_num[0]) : 1.0;
+  __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;
   const int64_t i = t / k;
   const int j = (int)(t - i * k);
   const Philox4 r = philox4x32_10((uint32_t)j, (uint32_t)i, (uint32_t)(i >> 32), TAG_INIT, k0, k1);
   double v = (double)r.x0 * 0x1p-32;
-  if (scale_num) v *= scale_mul * sqrt(scale_num[0]);
+  if (scale_num) v *= scale;
   out[t] = (float)v;
 }
 

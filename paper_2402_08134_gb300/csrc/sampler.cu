@@ -110,12 +110,17 @@ __global__ void __launch_bounds__(1024) sample_scan(int nblk, int* blk_cnt, unsi
     oc += vc;
     oq += vq;
   }
+  // theta and the non-kept mass: each thread's blocks in order, then a fixed
+  // tree (deterministic; a serial FP64 loop over all blocks was slow here)
+  __shared__ double sh[32];
+  double th = 0.0, ms = 0.0;
+  for (int b = b0; b < b1; ++b) {
+    th += blk_theta[b];
+    ms += blk_mass[b];
+  }
+  th = block_sum(th, sh);
+  ms = block_sum(ms, sh);
   if (t == 0) {
-    double th = 0.0, ms = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      th += blk_theta[b];
-      ms += blk_mass[b];
-    }
     const int sD = sc[1023];
     const unsigned long long T = sq[1023];
     int sR = (T > 0ull) ? max(s - sD, 0) : 0;

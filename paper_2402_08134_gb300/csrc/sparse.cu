@@ -1,7 +1,8 @@
 // Sparse and sampled products with X.
-//   csr_xf          : Y = X F, one warp per CSR row, each lane owning VPL
-//                     consecutive columns of F (vector loads of F rows when
-//                     the rows are aligned for them, scalar loads otherwise).
+//   csr_xf          : Y = X F, a warp (half a warp for N <= 16) per CSR row,
+//                     each lane owning VPL consecutive columns of F (vector
+//                     loads of F rows when aligned for them, scalar loads
+//                     otherwise).
 //   csr_sampled_xf  : Y += X S^T S F of Alg. LvS-SymNMF: for every sampled
 //                     row i (weight w) and nonzero (i, c, x): Y[c,:] += w x F[i,:]
 //                     (X symmetric, so sampled columns are sampled rows).
@@ -13,49 +14,76 @@
 
 namespace symnmf {
 
-template <int VPL, bool VEC>
+constexpr int CSR_BATCH = 8;
+
+// Y = X F for CSR X: LPR lanes per row (32: a warp, 16: half a warp), each
+// lane owning VPL consecutive columns.  The column indices and values of up to
+// LPR nonzeros are loaded at once (streaming: they are read once) and handed
+// round by shuffles; CSR_BATCH gathers of F rows are in flight per lane group
+// before their FMAs.
+template <int LPR, int VPL, bool VEC>
 __global__ void __launch_bounds__(256) csr_xf_kernel(const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col,
                                                      const float* __restrict__ val, int64_t n,
                                                      const float* __restrict__ F, int ldf, int N,
                                                      float* __restrict__ Y, int ldy) {
+  constexpr int RPW = 32 / LPR;  // rows per warp
   const int lane = threadIdx.x & 31;
+  const int li = lane % LPR;
+  const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (lane - li));
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int c0 = lane * VPL;
-  for (int64_t r = warp; r < n; r += nwarps) {
+  const int c0 = li * VPL;
+  for (int64_t r = warp * RPW + lane / LPR; r < n; r += nwarps * RPW) {
     float acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) acc[v] = 0.f;
     const int64_t b = rp[r], e = rp[r + 1];
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      const int64_t p = p0 + lane;
+    for (int64_t p0 = b; p0 < e; p0 += LPR) {
+      const int64_t p = p0 + li;
       int cc = 0;
       float xv = 0.f;
       if (p < e) {
-        cc = __ldg(col + p);
-        xv = __ldg(val + p);
+        cc = __ldcs(col + p);
+        xv = __ldcs(val + p);
       }
-      const int cnt = (int)std::min<int64_t>(32, e - p0);
-      for (int t = 0; t < cnt; ++t) {
-        const int c = __shfl_sync(0xffffffffu, cc, t);
-        const float x = __shfl_sync(0xffffffffu, xv, t);
-        const float* fr = F + (int64_t)c * ldf;
-        if (VEC && VPL == 4 && c0 + 3 < N) {
-          const float4 f = __ldg((const float4*)(fr + c0));
-          acc[0] = fmaf(x, f.x, acc[0]);
-          acc[1] = fmaf(x, f.y, acc[1]);
-          acc[2] = fmaf(x, f.z, acc[2]);
-          acc[3] = fmaf(x, f.w, acc[3]);
-        } else if (VEC && VPL == 2 && c0 + 1 < N) {
-          const float2 f = __ldg((const float2*)(fr + c0));
-          acc[0] = fmaf(x, f.x, acc[0]);
-          acc[1] = fmaf(x, f.y, acc[1]);
-        } else {
+      const int cnt = (int)std::min<int64_t>(LPR, e - p0);
+      for (int t0 = 0; t0 < cnt; t0 += CSR_BATCH) {
+        float fv[CSR_BATCH][VPL], xs[CSR_BATCH];
 #pragma unroll
-          for (int v = 0; v < VPL; ++v)
-            if (c0 + v < N) acc[v] = fmaf(x, __ldg(fr + c0 + v), acc[v]);
+        for (int u = 0; u < CSR_BATCH; ++u) {
+          const int t = t0 + u;  // < LPR: t0 <= LPR - CSR_BATCH
+          const int c = __shfl_sync(mask, cc, t, LPR);
+          xs[u] = __shfl_sync(mask, xv, t, LPR);
+          const float* fr = F + (int64_t)c * ldf + c0;
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) fv[u][v] = 0.f;
+          if (t < cnt) {
+            bool done = false;
+            if constexpr (VEC && VPL == 4) {
+              if (c0 + 3 < N) {
+                const float4 f = __ldg((const float4*)fr);
+                fv[u][0] = f.x, fv[u][1] = f.y, fv[u][2] = f.z, fv[u][3] = f.w;
+                done = true;
+              }
+            } else if constexpr (VEC && VPL == 2) {
+              if (c0 + 1 < N) {
+                const float2 f = __ldg((const float2*)fr);
+                fv[u][0] = f.x, fv[u][1] = f.y;
+                done = true;
+              }
+            }
+            if (!done) {
+#pragma unroll
+              for (int v = 0; v < VPL; ++v)
+                if (c0 + v < N) fv[u][v] = __ldg(fr + v);
+            }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < CSR_BATCH; ++u)
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) acc[v] = fmaf(xs[u], fv[u][v], acc[v]);
       }
     }
     float* yr = Y + r * ldy;
@@ -67,23 +95,28 @@ __global__ void __launch_bounds__(256) csr_xf_kernel(const int64_t* __restrict__
 
 cudaError_t csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                    const float* F, int ldf, int N, float* Y, int ldy, cudaStream_t st) {
+  if (N < 1 || N > 128) return cudaErrorInvalidValue;
   const int64_t warps = n;
   int grid = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (grid < 1) grid = 1;
+  if (N <= 16) {  // half a warp per row: no idle lanes
+    const int grid16 = std::max(1, (int)std::min<int64_t>((n * 16 + 255) / 256, (int64_t)num_sms() * 16));
+    csr_xf_kernel<16, 1, false><<<grid16, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const bool vec4 = (ldf % 4 == 0) && (((uintptr_t)F & 15) == 0);
   const bool vec2 = (ldf % 2 == 0) && (((uintptr_t)F & 7) == 0);
   if (N <= 32)
-    csr_xf_kernel<1, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+    csr_xf_kernel<32, 1, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
   else if (N <= 64 && vec2)
-    csr_xf_kernel<2, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+    csr_xf_kernel<32, 2, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
   else if (N <= 64)
-    csr_xf_kernel<2, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
-  else if (N <= 128 && vec4)
-    csr_xf_kernel<4, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
-  else if (N <= 128)
-    csr_xf_kernel<4, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+    csr_xf_kernel<32, 2, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
+  else if (vec4)
+    csr_xf_kernel<32, 4, true><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
   else
-    return cudaErrorInvalidValue;
+    csr_xf_kernel<32, 4, false><<<grid, 256, 0, st>>>(row_ptr, col, val, n, F, ldf, N, Y, ldy);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -103,7 +103,7 @@ def test_fp8_quantizer_and_bf16_convert(S):
 def test_csr_product(S):
     g = sbm_csr(n=5000, c=8, avg_deg=20, ratio=10, seed=1)
     Xs = sp.csr_matrix((g["val"].astype(np.float64), g["col"], g["row_ptr"]), shape=(5000, 5000))
-    for N in (16, 20, 50, 64, 74, 128):  # 50, 74: rows not aligned for vector loads
+    for N in (3, 16, 20, 50, 64, 74, 128):  # <= 16: half a warp per row; 50, 74: rows not aligned for vector loads
         F = uniform_factor(5000, N, seed=N)
         rp = torch.tensor(g["row_ptr"], device="cuda")
         col = torch.tensor(g["col"], device="cuda")
