@@ -163,10 +163,22 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def recorded_traffic(name, source):
-    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if it still matches the source."""
+# the files each profiled kernel is compiled from (its .cu and the headers it includes)
+PRODUCT_SOURCES = ("gemm_tc.cu", "tc_common.cuh", "common.cuh")
+ENGINE_SOURCES = ("lai_engine.cu", "hals_row.cuh", "persist.cuh", "common.cuh")
+
+
+def source_digest(sources):
+    """First 16 hex digits of the SHA-256 of the kernel's source files (csrc/), concatenated in order."""
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_2402_08134_gb300", "csrc", src), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name, sources):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if it still matches the sources."""
     path = os.path.join(ROOT, "profiles", name)
-    src = os.path.join(ROOT, "paper_2402_08134_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -174,7 +186,7 @@ def recorded_traffic(name, source):
         if "=" in line and not line.startswith("#"):
             a, b = line.split("=", 1)
             vals[a.strip()] = b.strip()
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = source_digest(sources)
     if vals.get("source_sha256_16") != digest:
         return None
     try:
@@ -449,7 +461,7 @@ def run_ours(args):
     roof_product = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F, N=l=50)", "bound": "hbm", "achieved": achieved,
                     "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
                     "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
-                    "traffic": recorded_traffic("xf_tc_bf16_n20000_traffic.txt", "gemm_tc.cu"),
+                    "traffic": recorded_traffic("xf_tc_bf16_n20000_traffic.txt", PRODUCT_SOURCES),
                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "launches": prod_n,
                     "tflops": (2.0 * N * N * L / (avg_launch_ms * 1e-3) / 1e12) if prod_n else None}
     # the dominant kernel of the step: the persistent LAI sweep launch (latency-bound FP32 arithmetic
@@ -462,7 +474,7 @@ def run_ours(args):
             "bound": "alu", "achieved": eng_achieved, "peak": fp32_pk,
             "peak_kind": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz", "unit": "TFLOP/s",
             "frac": (eng_achieved / fp32_pk) if eng_achieved else None,
-            "traffic": recorded_traffic("lai_resident_n20000_k20_l50_traffic.txt", "lai_engine.cu"),
+            "traffic": recorded_traffic("lai_resident_n20000_k20_l50_traffic.txt", ENGINE_SOURCES),
             "flops_per_launch": eng_flops_launch, "avg_launch_ms": eng_avg_ms, "launches": eng_n,
             "share_of_step": (eng_ms / args.steps) / ms_step if eng_n else None}
 

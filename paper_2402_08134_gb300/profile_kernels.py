@@ -35,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--nprob", type=int, default=16)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--time", action="store_true", help="print the mean time per run (CUDA events)")
     a = ap.parse_args(argv)
 
     import torch
@@ -130,9 +131,14 @@ def main(argv=None):
         run = lambda: (net.loss_grad(x, Hs), net.adam(1e-3))  # noqa: E731
     run()
     torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
     for _ in range(a.reps):
         out = run()
+    t1.record()
     torch.cuda.synchronize()
+    if a.time:
+        print(f"{a.case} n={n} k={a.k}: {t0.elapsed_time(t1) * 1e3 / max(a.reps, 1):.0f} us per run", flush=True)
     print(f"{a.case} n={n} done ({type(out).__name__}); launches={S.launch_count()}", flush=True)
     return 0 if math.isfinite(0.0) else 1
 
