@@ -84,18 +84,18 @@ constexpr int hals_split_stride() {
 }
 
 // One row split over NS adjacent lanes (the lane pair `mask`), part p owning
-// columns [p KMAX/NS, (p+1) KMAX/NS) of w and y in registers, zero padded past
-// k.  Gp4 points at this part's columns of G with the diagonal zeroed (row
+// columns [p KMAX/NS, (p+1) KMAX/NS) of w in registers (zero padded past k)
+// and reading its row of X F through `y_at(own index)` (zero past k).  Gp4 points at this part's columns of G with the diagonal zeroed (row
 // stride hals_split_stride), so every lane sums -w_j G_ij over its own j and
 // the parts' sums meet by one shuffle; the owner of column i then forms
 // w_i = max(0, (y_i + alpha h_i - sum_{j != i} w_j G_ij) / (G_ii + alpha))
 // (Eq. symhals_update2) with the fixed row's h_i from `fx_at(own index)`,
 // called for i < k only.  Adds the part's F_upd . Y and ||F_upd - F_fix||^2
 // to the double-float accumulators; returns true on a non-finite value.
-template <int KMAX, int NS, class FXA>
-__device__ __forceinline__ bool hals_row_split(float (&w)[KMAX / NS], const float (&y)[KMAX / NS], float alpha,
-                                               int k, int p, unsigned mask, const float4* Gp4, const float* inv,
-                                               FXA fx_at, float2& trv, float2& ddv) {
+template <int KMAX, int NS, class YA, class FXA>
+__device__ __forceinline__ bool hals_row_split(float (&w)[KMAX / NS], YA y_at, float alpha, int k, int p,
+                                               unsigned mask, const float4* Gp4, const float* inv, FXA fx_at,
+                                               float2& trv, float2& ddv) {
   constexpr int KH = KMAX / NS;
   constexpr int RS4 = hals_split_stride<KMAX, NS>() / 4;
   bool bad = false;
@@ -116,11 +116,12 @@ __device__ __forceinline__ bool hals_row_split(float (&w)[KMAX / NS], const floa
     if (p == i / KH) {
       const int ii = i % KH;
       const float hi = i < k ? fx_at(ii) : 0.f;
-      const float wi = fmaxf((y[ii] + fmaf(alpha, hi, s)) * inv[i], 0.f);  // padded columns: inv = 0
+      const float yi = y_at(ii);
+      const float wi = fmaxf((yi + fmaf(alpha, hi, s)) * inv[i], 0.f);  // padded columns: inv = 0
       w[ii] = wi;
       if (!isfinite(wi)) bad = true;
       const float d = wi - hi;
-      t[i & 1] = fmaf(wi, y[ii], t[i & 1]);
+      t[i & 1] = fmaf(wi, yi, t[i & 1]);
       d2[i & 1] = fmaf(d, d, d2[i & 1]);
     }
   }

@@ -535,8 +535,9 @@ constexpr int hals_ns() {
 // Full-X HALS update, Eq. symhals_update2:
 //   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
 // i = 0..k-1 in order with the columns already updated.  NS = hals_ns threads
-// per row, each holding its KMAX / NS columns of F_upd and of Y in registers
-// (zero padded; 16-byte loads when VEC); G with its diagonal zeroed and the
+// per row, each holding its KMAX / NS columns of F_upd in registers and of Y
+// in its own column of shared memory (zero padded; 16-byte loads when VEC);
+// G with its diagonal zeroed and the
 // reciprocals 1 / (G_ii + alpha) in shared memory, read as broadcasts.  With U
 // given the row of Y is formed in registers as U_r M (LAI, M = Lambda U^T F_fix
 // in shared memory).  Persistent grid over rows; F_upd . Y and
@@ -552,7 +553,8 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
   extern __shared__ __align__(16) float sm[];
   float* Gs = sm;               // KMAX x RS, diagonal zeroed
   float* inv = Gs + KMAX * RS;  // KMAX
-  float* Ms = inv + KMAX;       // l x KMAX (LAI only)
+  float* Ys = inv + KMAX;       // KH x HALS_THREADS: each thread's row of Y, column-major
+  float* Ms = Ys + KH * HALS_THREADS;  // l x KMAX (LAI only)
   const int tid = threadIdx.x;
   for (int e = tid; e < KMAX * KMAX; e += HALS_THREADS) {
     const int i = e / KMAX, j = e - i * KMAX;
@@ -574,8 +576,9 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
   const float4* Ms4 = reinterpret_cast<const float4*>(Ms + c0);
   float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
   bool bad = false;
+  float* ys = Ys + tid;  // this thread's column: y_c at ys[c * HALS_THREADS] (no bank conflicts)
   for (int64_t r = (int64_t)blockIdx.x * RPB + tid / NS; r < n; r += (int64_t)gridDim.x * RPB) {
-    float y[KH], w[KH];
+    float w[KH];
     float* fu = Fu + r * k + c0;
     const float* fx = Ff + r * k + c0;
     if constexpr (VEC) {
@@ -589,7 +592,9 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
 #pragma unroll
       for (int c = 0; c < KH; ++c) w[c] = c0 + c < k ? __ldg(fu + c) : 0.f;
     }
+    // this row of Y into shared memory (read once per column there: fewer registers)
     if (U) {  // Y_r = U_r M (LAI product fused into the update)
+      float y[KH];
 #pragma unroll
       for (int c = 0; c < KH; ++c) y[c] = 0.f;
       const float* ur = U + r * l;
@@ -605,21 +610,26 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
           y[4 * q + 3] = fmaf(u, m.w, y[4 * q + 3]);
         }
       }
+#pragma unroll
+      for (int c = 0; c < KH; ++c) ys[c * HALS_THREADS] = y[c];
     } else if constexpr (VEC) {
       const float* yr = Y + r * ldy + c0;
 #pragma unroll
       for (int q = 0; q < KH / 4; ++q) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c0 + 4 * q < k) v = __ldg(reinterpret_cast<const float4*>(yr) + q);
-        y[4 * q] = v.x, y[4 * q + 1] = v.y, y[4 * q + 2] = v.z, y[4 * q + 3] = v.w;
+        ys[(4 * q) * HALS_THREADS] = v.x, ys[(4 * q + 1) * HALS_THREADS] = v.y;
+        ys[(4 * q + 2) * HALS_THREADS] = v.z, ys[(4 * q + 3) * HALS_THREADS] = v.w;
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < KH; ++c) y[c] = c0 + c < k ? __ldg(Y + r * ldy + c0 + c) : 0.f;
+      for (int c = 0; c < KH; ++c) ys[c * HALS_THREADS] = c0 + c < k ? __ldg(Y + r * ldy + c0 + c) : 0.f;
     }
-    // the fixed row is read column by column (L1 hits after the first)
-    bad |= hals_row_split<KMAX, NS>(w, y, alpha, k, p, mask, Gp4, inv, [&](int c) { return __ldg(fx + c); }, trv,
-                                    ddv);
+    // the fixed row is read column by column (L1 hits after the first); the
+    // shared-memory column of Y is this thread's own, so no barrier is needed
+    bad |= hals_row_split<KMAX, NS>(
+        w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, p, mask, Gp4, inv,
+        [&](int c) { return __ldg(fx + c); }, trv, ddv);
     if constexpr (VEC) {
 #pragma unroll
       for (int q = 0; q < KH / 4; ++q)
@@ -649,7 +659,8 @@ template <int KMAX, bool VEC>
 static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, const float* G, double alpha,
                                const float* Y, int ldy, const float* U, int l, const float* M, double* part,
                                double* ws, unsigned* counter, unsigned* err, cudaStream_t st) {
-  size_t smem = (size_t)(KMAX * hals_split_stride<KMAX, hals_ns<KMAX>()>() + KMAX) * 4;
+  size_t smem = (size_t)(KMAX * hals_split_stride<KMAX, hals_ns<KMAX>()>() + KMAX +
+                         (KMAX / hals_ns<KMAX>()) * HALS_THREADS) * 4;
   if (U) smem += (size_t)l * KMAX * 4;
   auto kern = hals_kernel<KMAX, VEC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
