@@ -17,11 +17,18 @@ solution's residual against the FP32 X is compared with the FP64 oracle's
 residual after 200 plain sweeps (stored in tests/golden/c2_reference.json):
 it must be within 1e-3.
 
-Also reported: the plain FP32 form (FP32 X, full X.H every sweep, 200 sweeps,
-same start) timed the same way, the end-to-end time through the public API
-with X copied in from pinned host memory, the live roofline of the tcgen05
-product kernel, SM clocks sampled during the timed region, and the oracle
-timed on the host cores.  `--impl reference` times the oracle itself.
+Also reported:
+- the plain FP32 form (FP32 X, full X.H every sweep, 200 sweeps, same start),
+  timed the same way;
+- the end-to-end time through the public API, with X copied in from pinned
+  host memory;
+- the live rooflines of the LAI sweep launch and of the tcgen05 product kernel;
+- the other forms (unless --no-forms): FP8 X, the product at N = 256, the
+  batched grouped solver, and the learned warm start at reduced size;
+- SM clocks sampled during the timed region;
+- the oracle timed on the host cores.
+
+`--impl reference` times the oracle itself.
 
 Multi-GPU: the method does not shard at these sizes; each rank solves its own
 replica of the workload (independent replicas, weak scaling) and rank 0
@@ -202,6 +209,30 @@ def fp32_peak_tflops(dev, clk):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def learned_form():
+    """The learned warm start at reduced size: 16 Gaussian-mixture instances (n = 3000 in R^16, 8
+    components, k = 8, l = 26) solved by the library train the network (20 epochs of its kernels);
+    on 3 held-out instances the learned and the random start run 60 LAI sweeps each, and the sweeps
+    each needs to reach the objective the random start ends at are reported."""
+    from paper_2402_08134_gb300 import warmstart as WS
+
+    out = WS.experiment(n=3000, d=16, c=8, k=8, l=26, q=2, sweeps=60, n_train=16, n_test=3, epochs=20, lr=2e-3,
+                        train_seeds=500, test_seeds=0)
+    rows = out["rows"]
+    pick = lambda name, key: [r[name][key] for r in rows]  # noqa: E731
+    return {
+        "config": "warm-start workload at reduced size: n=3000, d=16, c=8 (Dirichlet weights), k=8, l=26, "
+                  "16 training instances, 3 held-out, 60 LAI sweeps",
+        "sweeps_to_random_final": {"random": pick("random", "sweeps_to_target"),
+                                   "learned": pick("learned", "sweeps_to_target")},
+        "obj_after_5_sweeps": {"random": pick("random", "obj5"), "learned": pick("learned", "obj5")},
+        "nr_final": {"random": pick("random", "nr"), "learned": pick("learned", "nr")},
+        "solve_s": {"random": pick("random", "seconds"), "learned": pick("learned", "seconds")},
+        "train_s": out["t_train"],
+        "loss_first_last": [out["losses"][0], out["losses"][-1]],
+    }
 
 
 def batched_form(S, dev, sweeps=100, sample_every=8):
@@ -404,8 +435,9 @@ def run_ours(args):
         out["fp8"] = {"s": a.elapsed_time(b) / 1e3 / args.steps, "nr": s8.residual(S.SRC_XHI)[0],
                       "reached_target": (s8.residual(S.SRC_XHI)[0] <= target) if target else None}
         s8.close()
-        # the product kernel at a width past the BF16 ridge (N = 256, 256 flop per byte of BF16 X),
-        # timed alone (kernel events), against the measured burst peak of its dtype
+        # the product kernel at a width near the BF16 ridge (N = 256: 256 flop per byte of BF16 X,
+        # against a measured ridge of ~279), timed alone (kernel events), against the measured
+        # burst peak of its dtype
         pk_t, _ = peaks()
         Fw = torch.rand((N, 256), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
         tens = {}
@@ -425,6 +457,7 @@ def run_ours(args):
         out["tensor_n256"] = dict(tens, shape=f"n={N}, N=256 (xf_tc_kernel<256, 256-row tiles>)")
         del x8, rs8, Fw
         out["batched_c4"] = batched_form(S, dev)
+        out["learned_small"] = learned_form()
 
     # end to end through the public API: X from pinned host memory, result back to host
     Xh = Xb.cpu().pin_memory()
