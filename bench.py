@@ -172,7 +172,7 @@ def peaks():
 
 # the files each profiled kernel is compiled from (its .cu and the headers it includes)
 PRODUCT_SOURCES = ("gemm_tc.cu", "tc_common.cuh", "common.cuh")
-ENGINE_SOURCES = ("lai_engine.cu", "hals_row.cuh", "persist.cuh", "common.cuh")
+ENGINE_SOURCES = ("lai_engine.cuh", "lai_engine_narrow.cu", "hals_row.cuh", "persist.cuh", "common.cuh")
 
 
 def source_digest(sources):

@@ -86,6 +86,18 @@ SYMNMF_D T block_sum(T v, T* sh /* >= 32 entries */) {
   return r;
 }
 
+// Last-block-done reduction of per-block partials: no block ever waits.
+template <int NV>
+__device__ inline bool last_block(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
 SYMNMF_D void set_error(unsigned* err, unsigned bit) {
   if (err) atomicOr(err, bit);
 }
