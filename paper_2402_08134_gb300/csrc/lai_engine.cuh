@@ -259,7 +259,13 @@ __device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, c
 // sums go to fin[side] (both (i, j) and (j, i) for F^T F), the FP32 state of the
 // next half to state[side], and after the H half of sweep t >= 0 this CTA's
 // objective share to objp[t].
-constexpr int LE_BATCH = 32;
+// Records are read as float4 runs, LE_BATCH per thread in flight; a chunk of
+// at most LE_CHUNK positions is reduced at a time.  red holds the group sums
+// (2 floats per position and group: at most 2 LE_THREADS float4s) and, from
+// LE_STAGE on, the chunk's final (hi, lo) pairs.
+constexpr int LE_BATCH = 8;
+constexpr int LE_CHUNK = 4 * 64;
+constexpr int LE_STAGE = 8 * LE_THREADS;
 
 __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int t, float* red, double* shd) {
   const int k = a.k, l = a.l, k4 = (k + 3) & ~3, gp = a.gp;
@@ -268,36 +274,63 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
   const unsigned nrec = gridDim.x * le_row_groups(l, k);
   double* fin = a.fin + side * E;
   float* st = a.state + side * SL;
-  // positions per CTA, even: the hi/lo pairs of tr and dd (at EP - 4, EP - 2) never straddle two CTAs
-  const int per = ((EP + gridDim.x - 1) / gridDim.x + 1) & ~1;
+  // positions per CTA, a multiple of 4: float4 runs of a record, and the hi/lo
+  // pairs of tr and dd (at EP - 4, EP - 2; EP is a multiple of 4) never straddle two CTAs
+  const int per = ((EP + gridDim.x - 1) / gridDim.x + 3) & ~3;
   const int c0 = blockIdx.x * per, c1 = min(EP, c0 + per);
   double share = 0.0;
-  for (int i0 = c0; i0 < c1; i0 += LE_THREADS) {  // chunks of at most LE_THREADS positions
-    const int np = min(LE_THREADS, c1 - i0);
-    const int S = LE_THREADS / np;  // record strides
-    const int pos = threadIdx.x % np, g = threadIdx.x / np;
-    const int idx = i0 + pos;
-    float hi = 0.f, lo = 0.f;
+  for (int i0 = c0; i0 < c1; i0 += LE_CHUNK) {  // chunks of at most LE_CHUNK positions
+    const int np = min(LE_CHUNK, c1 - i0);
+    const int nc = (np + 3) / 4;        // float4 columns of the chunk
+    const int S = LE_THREADS / nc;      // record groups (>= 4)
+    const int col = threadIdx.x % nc, g = threadIdx.x / nc;
+    // group g sums records g, g + S, ... of its column in double-float
     if (g < S) {
+      float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* src = a.part + i0 + 4 * col;  // i0 + 4 col < EP: the run stays in its record
       for (unsigned q0 = g; q0 < nrec; q0 += (unsigned)S * LE_BATCH) {
-        float v[LE_BATCH];
+        float4 v[LE_BATCH];
 #pragma unroll
         for (int u = 0; u < LE_BATCH; ++u) {
           const unsigned q = q0 + (unsigned)S * u;
-          v[u] = q < nrec ? __ldcg(a.part + (size_t)q * EP + idx) : 0.f;
+          v[u] = q < nrec ? __ldcg(reinterpret_cast<const float4*>(src + (size_t)q * EP))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < LE_BATCH; ++u) df_add(hi, lo, v[u], 0.f);
+        for (int u = 0; u < LE_BATCH; ++u) {
+          df_add(hi[0], lo[0], v[u].x, 0.f);
+          df_add(hi[1], lo[1], v[u].y, 0.f);
+          df_add(hi[2], lo[2], v[u].z, 0.f);
+          df_add(hi[3], lo[3], v[u].w, 0.f);
+        }
       }
-      red[2 * (g * np + pos)] = hi;
-      red[2 * (g * np + pos) + 1] = lo;
+      float4* r4 = reinterpret_cast<float4*>(red) + 2 * (g * nc + col);
+      r4[0] = make_float4(hi[0], lo[0], hi[1], lo[1]);
+      r4[1] = make_float4(hi[2], lo[2], hi[3], lo[3]);
     }
     __syncthreads();
-    if (threadIdx.x < np) {
-      float h = 0.f, o = 0.f;
-      for (int gg = 0; gg < S; ++gg) df_add(h, o, red[2 * (gg * np + threadIdx.x)], red[2 * (gg * np + threadIdx.x) + 1]);
-      red[2 * LE_THREADS + 2 * threadIdx.x] = h;  // stage for the pairs of tr, dd
-      red[2 * LE_THREADS + 2 * threadIdx.x + 1] = o;
+    // the S group sums of each column by a fixed tree (deterministic)
+    for (int sg = 1; sg < S; sg <<= 1) {
+      if (g < S && (g & (2 * sg - 1)) == 0 && g + sg < S) {
+        float4* r4 = reinterpret_cast<float4*>(red) + 2 * (g * nc + col);
+        const float4* o4 = reinterpret_cast<const float4*>(red) + 2 * ((g + sg) * nc + col);
+        float4 x0 = r4[0], x1 = r4[1];
+        const float4 y0 = o4[0], y1 = o4[1];
+        df_add(x0.x, x0.y, y0.x, y0.y);
+        df_add(x0.z, x0.w, y0.z, y0.w);
+        df_add(x1.x, x1.y, y1.x, y1.y);
+        df_add(x1.z, x1.w, y1.z, y1.w);
+        r4[0] = x0;
+        r4[1] = x1;
+      }
+      __syncthreads();
+    }
+    const int idx = i0 + (int)threadIdx.x;
+    if ((int)threadIdx.x < np) {
+      // group 0 holds column c's four sums as (hi, lo) pairs: position 4 c + e at red[8 c + 2 e]
+      const float h = red[2 * threadIdx.x], o = red[2 * threadIdx.x + 1];
+      red[LE_STAGE + 2 * threadIdx.x] = h;  // stage for the pairs of tr, dd
+      red[LE_STAGE + 2 * threadIdx.x + 1] = o;
       const double v = (double)h + (double)o;
       if (idx < EP - 4) {
         const int tile = idx >> 4, p = (idx >> 2) & 3, q = idx & 3;
@@ -326,9 +359,9 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
     __syncthreads();
     // tr and dd: hi/lo pairs at positions EP - 4 .. EP - 1
     if (threadIdx.x < np && (idx == EP - 4 || idx == EP - 2)) {
-      float h = red[2 * LE_THREADS + 2 * threadIdx.x], o = red[2 * LE_THREADS + 2 * threadIdx.x + 1];
+      float h = red[LE_STAGE + 2 * threadIdx.x], o = red[LE_STAGE + 2 * threadIdx.x + 1];
       if (threadIdx.x + 1 < np) {
-        df_add(h, o, red[2 * LE_THREADS + 2 * threadIdx.x + 2], red[2 * LE_THREADS + 2 * threadIdx.x + 3]);
+        df_add(h, o, red[LE_STAGE + 2 * threadIdx.x + 2], red[LE_STAGE + 2 * threadIdx.x + 3]);
         const double v = (double)h + (double)o;
         const int e = lk + k * k + (idx == EP - 4 ? 0 : 1);
         fin[e] = v;
