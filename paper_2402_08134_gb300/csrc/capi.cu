@@ -69,11 +69,52 @@ static symnmf_status cuda_fail(symnmf_t h, cudaError_t e, const char* where) {
     if (_s != SYMNMF_OK) return _s;      \
   } while (0)
 
+// Handle memory comes from a library-owned stream-ordered pool per device:
+// creating and destroying handles then neither maps fresh memory nor
+// synchronises the device (cudaFree does), and up to 1 GiB of freed handle
+// memory stays cached for the next handle.  Without a pool, the device's
+// default pool is used.
+static cudaMemPool_t handle_pool() {
+  constexpr int MAXDEV = 64;
+  static std::mutex mu;
+  static cudaMemPool_t pools[MAXDEV] = {};
+  static bool tried[MAXDEV] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pools[dev], &props) == cudaSuccess) {
+      uint64_t keep = (uint64_t)1 << 30;
+      cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      pools[dev] = nullptr;
+      cudaGetLastError();
+    }
+  }
+  return pools[dev];
+}
+
+// Device memory owned by the handle: stream-ordered on the handle's stream,
+// except while a sweep is being captured into a graph (an allocation there
+// would become a graph node), where plain cudaMalloc is used.
 template <typename T>
 static cudaError_t dalloc(symnmf_t h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e;
+  if (h->capturing) {
+    e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) h->allocs_sync.push_back((void*)*p);
+    return e;
+  }
+  cudaMemPool_t pool = handle_pool();
+  e = pool ? cudaMallocFromPoolAsync((void**)p, bytes, pool, h->st) : cudaMallocAsync((void**)p, bytes, h->st);
   if (e == cudaSuccess) h->allocs.push_back((void*)*p);
   return e;
 }
@@ -344,7 +385,8 @@ extern "C" void symnmf_destroy(symnmf_t h) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->st);  // after the handle's work on its stream
+  for (void* p : h->allocs_sync) cudaFree(p);
   delete h;
 }
 

@@ -43,7 +43,8 @@ struct symnmf_ctx {
   int k = 0;
   double alpha = 0.0, normX2 = 0.0;
   std::string msg;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;       // stream-ordered (pool) allocations, freed on st
+  std::vector<void*> allocs_sync;  // plain cudaMalloc (made while capturing)
 
   float *H = nullptr, *W = nullptr, *Y = nullptr;
   double* Gd[2] = {nullptr, nullptr};  // [0] H^T H, [1] W^T W (FP64)
