@@ -25,7 +25,8 @@
  *     which case it synchronises that stream.
  *   - Borrowed memory (X, CSR arrays, scales, caller buffers) stays owned by
  *     the caller and must outlive the handle / the call.  The handle owns its
- *     factors, sketch and workspaces (allocated with cudaMalloc at create).
+ *     factors, sketch and workspaces (allocated at create, stream-ordered on the
+ *     handle's stream from a library-owned memory pool; freed in stream order at destroy).
  *   - Errors are returned as symnmf_status; no call throws or aborts.  A
  *     failing call leaves a message in symnmf_last_error(handle).  Kernel
  *     waits are bounded: a wait that runs out sets a device error word that
@@ -48,7 +49,7 @@ typedef struct symnmf_mlp_ctx* symnmf_mlp_t;
 typedef enum {
   SYMNMF_OK = 0,
   SYMNMF_EINVAL = 1,      /* bad argument (size, pointer, format, alignment) */
-  SYMNMF_ENOMEM = 2,      /* cudaMalloc failed */
+  SYMNMF_ENOMEM = 2,      /* a device allocation failed */
   SYMNMF_ENOTSPD = 3,     /* a Gram matrix that must be positive definite is not */
   SYMNMF_ETIMEOUT = 4,    /* a bounded device wait ran out */
   SYMNMF_ENAN = 5,        /* a non-finite value reached a factor or objective */
