@@ -24,12 +24,12 @@ constexpr int hals_ns() {
 //   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
 // i = 0..k-1 in order with the columns already updated.  NS = hals_ns threads
 // per row, each holding its KMAX / NS columns of F_upd in registers and of Y
-// in its own column of shared memory (zero padded; 16-byte loads when VEC);
-// G with its diagonal zeroed and the
-// reciprocals 1 / (G_ii + alpha) in shared memory, read as broadcasts.  With U
-// given the row of Y is formed in registers as U_r M (LAI, M = Lambda U^T F_fix
-// in shared memory).  Persistent grid over rows; F_upd . Y and
-// ||F_upd - F_fix||^2 are kept per thread in double-float and reduced in FP64.
+// in its own column of shared memory (zero padded; 16-byte loads when VEC).
+// G with its diagonal zeroed and the reciprocals 1 / (G_ii + alpha) sit in
+// shared memory, read as broadcasts.  With U given, the row of Y is formed as
+// U_r M (LAI, M = Lambda U^T F_fix in shared memory).  Persistent grid over
+// rows; F_upd . Y and ||F_upd - F_fix||^2 are kept per thread in double-float
+// and reduced in FP64.
 template <int KMAX, bool VEC>
 __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
     float* __restrict__ Fu, const float* __restrict__ Ff, int64_t n, int k, const float* __restrict__ G, float alpha,
