@@ -26,7 +26,8 @@
  *   - Borrowed memory (X, CSR arrays, scales, caller buffers) stays owned by
  *     the caller and must outlive the handle / the call.  The handle owns its
  *     factors, sketch and workspaces (allocated at create, stream-ordered on the
- *     handle's stream from a library-owned memory pool; freed in stream order at destroy).
+ *     handle's stream from a library-owned memory pool; freed in stream order at
+ *     destroy, so the handle's stream must outlive the handle).
  *   - Errors are returned as symnmf_status; no call throws or aborts.  A
  *     failing call leaves a message in symnmf_last_error(handle).  Kernel
  *     waits are bounded: a wait that runs out sets a device error word that
