@@ -468,10 +468,13 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
 
 // Rank-safe orthonormalisation of S (n x l) in place, T scratch (n x l):
 // shifted CholeskyQR3 (cholqr.cu), one cooperative launch unless the handle
-// asks for separate kernels per step.
-static symnmf_status orth(symnmf_t h, float* S, float* T, int l) {
+// asks for separate kernels per step.  The range finder's intermediate bases
+// only carry the span to the next product with X, so they stop after two
+// passes (well conditioned, orthonormal to ~1e-4); the final basis, which
+// Apx-EVD rotates into U, takes all three.
+static symnmf_status orth(symnmf_t h, float* S, float* T, int l, bool final_basis) {
   TRY(cholqr3(S, T, h->n, l, h->cq_part, h->cq_fin, h->Sm_d, h->cq_Rf, h->cq_rinv, h->ws, h->counters + 0,
-              h->eng_bar, h->err, h->o.lai_mode != 1, h->st));
+              h->eng_bar, h->err, h->o.lai_mode != 1, h->st, final_basis ? 3 : 2));
   return SYMNMF_OK;
 }
 
@@ -488,12 +491,12 @@ extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float
   float* A = h->Qa;
   float* B = h->Qb;
   TRYS(product(h, SYMNMF_SRC_X, h->Om, l, l, A, l));  // Y = X Omega
-  TRYS(orth(h, A, B, l));
+  TRYS(orth(h, A, B, l, q == 0));
   for (int j = 0; j < q; ++j) {
     TRYS(product(h, SYMNMF_SRC_X, A, l, l, B, l));  // X^T Q (= X Q)
-    TRYS(orth(h, B, A, l));
+    TRYS(orth(h, B, A, l, false));
     TRYS(product(h, SYMNMF_SRC_X, B, l, l, A, l));  // X Q
-    TRYS(orth(h, A, B, l));
+    TRYS(orth(h, A, B, l, j == q - 1));
   }
   // Apx-EVD: T = Q^T X Q, T = V Lambda V^T, U = Q V
   TRYS(product(h, SYMNMF_SRC_X, A, l, l, B, l));
@@ -554,6 +557,17 @@ static symnmf_status validate_sweep(symnmf_t h, int src, int rule) {
   if (rule != SYMNMF_RULE_HALS && rule != SYMNMF_RULE_BPP) return fail(h, SYMNMF_EINVAL, "bad rule");
   return SYMNMF_OK;
 }
+
+// A captured sweep graph for (src, rule) at the current sketch, or nullptr.
+static symnmf_ctx::Graph* cached_graph(symnmf_t h, int src, int rule) {
+  for (auto& g : h->graphs)
+    if (g.exec && g.src == src && g.rule == rule && g.lai_version == h->lai_version) return &g;
+  return nullptr;
+}
+
+// Capturing and instantiating a graph costs about as much as a few eager
+// sweeps: a new graph is made only when at least this many replays follow.
+constexpr int GRAPH_MIN_REPLAYS = 4;
 
 static symnmf_status get_graph(symnmf_t h, int src, int rule, symnmf_ctx::Graph** out) {
   for (auto& g : h->graphs)
@@ -657,7 +671,7 @@ extern "C" symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, 
     const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
     TRY(cudaMemsetAsync(h->obj_cnt, 0, sizeof(int), h->st));
     int t = 0;
-    if (h->o.use_graph) {
+    if (h->o.use_graph && (chunk >= 1 + GRAPH_MIN_REPLAYS || cached_graph(h, source, rule))) {
       if (!warmed) {
         // first sweep eagerly: workspaces get sized outside capture
         TRYS(sweep_body(h, source, rule));

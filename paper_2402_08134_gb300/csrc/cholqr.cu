@@ -100,6 +100,7 @@ struct CqArgs {
   dfl* fin;        // [l * l]
   unsigned* bar;   // barrier counter, zeroed
   unsigned* err;
+  int npass;       // 3: shifted CholeskyQR3; 2: the shifted pass and one plain pass
 };
 
 constexpr int CQ_BATCH = 16;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
   __syncthreads();
 
   unsigned epoch = 0;
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < a.npass; ++pass) {
     // partial Gram of this CTA's rows: 4x4 upper tiles, four rows per float4 step
     for (int w = tid; w < T * RG; w += CQ_THREADS) {
       const int tile = w % T, rg = w / T;
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(128) trsm_rows_kernel(const float* __restrict_
 size_t cholqr_part_doubles(int l) { return (size_t)num_sms() * cq_row_groups(l) * l * l; }
 
 template <int LMAX>
-static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G,
+static cudaError_t cholqr_run(int npass, float* S, float* T, int64_t n, int l, double* part, double* fin, double* G,
                               float* Rf, float* rinv, double* ws, unsigned* counter, unsigned* bar,
                               unsigned* err, bool allow_engine, cudaStream_t st) {
   int dev = 0, optin = 0;
@@ -344,7 +345,7 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
       if (e != cudaSuccess) return e;
       // the double-typed buffers hold double-float pairs (same size)
       CqArgs a{S, n, l, (int)rp, (int)(((rp + 7) & ~7LL) + 32), reinterpret_cast<dfl*>(part),
-               reinterpret_cast<dfl*>(fin), bar, err};
+               reinterpret_cast<dfl*>(fin), bar, err, npass};
       void* params[] = {&a};
       e = cudaLaunchCooperativeKernel((const void*)cholqr_engine_kernel<LMAX>, dim3(grid), dim3(CQ_THREADS),
                                       params, smem, st);
@@ -362,7 +363,7 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
   const size_t tsmem = (size_t)(l * l4 + l4) * 4;
   e = cudaFuncSetAttribute(trsm_rows_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
   if (e != cudaSuccess) return e;
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < npass; ++pass) {
     e = xcross(src, l, l, src, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, counter, st);
     if (e != cudaSuccess) return e;
     chol_factor_kernel<<<1, 256, fsmem, st>>>(G, l, cq_shift(pass), cq_drop(pass), Rf, rinv);
@@ -372,21 +373,22 @@ static cudaError_t cholqr_run(float* S, float* T, int64_t n, int l, double* part
     if (e != cudaSuccess) return e;
     std::swap(src, dst);
   }
-  // three passes leave the result in T
+  // an odd pass count leaves the result in T
+  if (src == S) return cudaSuccess;
   return cudaMemcpyAsync(S, src, (size_t)n * l * sizeof(float), cudaMemcpyDeviceToDevice, st);
 }
 
 cudaError_t cholqr3(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G, float* Rf,
                     float* rinv, double* ws, unsigned* counter, unsigned* bar, unsigned* err, bool allow_engine,
-                    cudaStream_t st) {
-  if (n < 1 || l < 1 || l > 96) return cudaErrorInvalidValue;
+                    cudaStream_t st, int npass) {
+  if (n < 1 || l < 1 || l > 96 || npass < 2 || npass > 3) return cudaErrorInvalidValue;
   if (l <= 32)
-    return cholqr_run<32>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+    return cholqr_run<32>(npass, S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
   if (l <= 64)
-    return cholqr_run<64>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+    return cholqr_run<64>(npass, S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
   if (l <= 80)
-    return cholqr_run<80>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
-  return cholqr_run<96>(S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+    return cholqr_run<80>(npass, S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
+  return cholqr_run<96>(npass, S, T, n, l, part, fin, G, Rf, rinv, ws, counter, bar, err, allow_engine, st);
 }
 
 }  // namespace symnmf

@@ -161,10 +161,12 @@ double lai_engine_flops(int64_t n, int k, int l, int nsweeps);
 // Shifted CholeskyQR3 of S (n x l, l <= 96) in place; T is n x l scratch for
 // the multi-kernel form (see cholqr.cu).  part: cholqr_part_doubles(l);
 // fin, G: l * l doubles; Rf: l * (l + 3) floats; rinv: l + 3 floats.
+// npass = 2 stops after the shifted pass and one plain pass: a basis of the
+// same span that is well conditioned but orthonormal only to ~1e-4.
 size_t cholqr_part_doubles(int l);
 cudaError_t cholqr3(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G, float* Rf,
                     float* rinv, double* ws, unsigned* counter, unsigned* bar, unsigned* err, bool allow_engine,
-                    cudaStream_t st);
+                    cudaStream_t st, int npass = 3);
 
 // -------------------------------------------------------------------- BPP
 cudaError_t bpp_rows(float* F_upd, const float* F_fix, int64_t n, int k, const double* G,
