@@ -187,7 +187,7 @@ cudaError_t jacobi_evd(const double* A, int l, double* V, double* lam, cudaStrea
   cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  jacobi_kernel<<<1, 512, smem, st>>>(A, l, V, lam);
+  jacobi_kernel<<<1, 1024, smem, st>>>(A, l, V, lam);
   count_launches(1);
   return cudaGetLastError();
 }
