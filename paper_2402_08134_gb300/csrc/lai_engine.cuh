@@ -110,34 +110,7 @@ __device__ __forceinline__ void le_tri(int g, int kt, int& bi, int& bj) {
   bj = b + g;
 }
 
-// Record position of final entry e (< l*k + k*k).
-__device__ __forceinline__ int le_rec_index(int e, int l, int k) {
-  const int kt = ((k + 3) & ~3) / 4, lk = l * k;
-  if (e < lk) {
-    const int i = e / k, j = e - i * k;
-    return ((i >> 2) * kt + (j >> 2)) * 16 + (i & 3) * 4 + (j & 3);
-  }
-  const int g = e - lk, i = g / k, j = g - i * k;
-  int bi = i >> 2, bj = j >> 2, p = i & 3, q = j & 3;
-  if (bi > bj) {
-    const int t = bi;
-    bi = bj;
-    bj = t;
-    const int u = p;
-    p = q;
-    q = u;
-  }
-  const int tm = (((l + 3) & ~3) / 4) * kt;
-  return (tm + le_tri_index(bi, bj, kt)) * 16 + p * 4 + q;
-}
-
 // Double-float accumulation (Dekker 1971, two-sum): (hi, lo) holds hi + lo.
-__device__ __forceinline__ void df_add_f(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bb = s - hi;
-  lo += (hi - (s - bb)) + (x - bb);
-  hi = s;
-}
 __device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
   const float s = hi + h2;
   const float bb = s - hi;
