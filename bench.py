@@ -1,34 +1,47 @@
 #!/usr/bin/env python3
 """Benchmark of the randomized SymNMF hot path on one GB300 (per rank).
 
-Workload (the LAI-SymNMF configuration): n = 20000 points of a 20-component
-Gaussian mixture in R^50, X_ij = exp(-||x_i - x_j||^2 / sigma^2) with sigma
-the median pairwise distance, k = 20, sketch width l = 2k + 10 = 50, q = 2
-power iterations, 200 sweeps, alpha = max(X).  X is generated on the device
-(synthetic data) and stored as BF16 (0.8 GB, larger than L2) for the
-tensor-core products and as FP32 for the plain form and the final check.
+Metric: time to the oracle's residual.  Workload (the LAI-SymNMF
+configuration): n = 20000 points of a 20-component Gaussian mixture in R^50,
+X_ij = exp(-||x_i - x_j||^2 / sigma^2) with sigma the median pairwise
+distance, k = 20, sketch width l = 2k + 10 = 50, q = 2 power iterations,
+alpha = max(X).  X is generated on the device (synthetic data) and stored as
+BF16 (0.8 GB, larger than L2) for the tensor-core products and as FP32 for the
+plain form and the final check.
 
-One step = one complete solve in the mixed form:
-  Philox start -> range finder with re-orthonormalisation on BF16 X
-  (6 tcgen05 passes over X) -> Apx-EVD -> 200 LAI sweeps (CUDA graph) ->
-  2 refinement sweeps with the full BF16 X -> residual against BF16 X.
-The metric is the step time in seconds (lower is better); after timing, the
-solution's residual against the FP32 X is compared with the FP64 oracle's
-residual after 200 plain sweeps (stored in tests/golden/c2_reference.json):
-it must be within 1e-3.
+Target: the FP64 oracle's normalized residual after the configuration's 200
+plain HALS sweeps (tests/golden/c2_reference.json, written by a script that
+calls only the oracle), plus 1e-3 for the BF16 / FP8 forms and times
+(1 + 1e-4) for FP32 forms.
 
-Also reported:
-- the plain FP32 form (FP32 X, full X.H every sweep, 200 sweeps, same start),
-  timed the same way;
-- the end-to-end time through the public API, with X copied in from pinned
-  host memory;
-- the live rooflines of the LAI sweep launch and of the tcgen05 product kernel;
-- the other forms (unless --no-forms): FP8 X, the product at N = 256, the
-  batched grouped solver, and the learned warm start at reduced size;
-- SM clocks sampled during the timed region;
-- the oracle timed on the host cores.
+One step = one solve to the target in the mixed form:
+  Philox start -> range finder with re-orthonormalisation on BF16 X (6
+  tcgen05 passes over X) -> Apx-EVD -> LAI-HALS sweeps in chunks of 10 (one
+  persistent launch per chunk), each chunk followed by a check of the
+  residual against X -> stop at the first check at or below the target;
+  should 200 LAI sweeps not reach it, full-X refinement sweeps (Iterative
+  Refinement) follow, checked after every 2.
+The in-loop checks use the handle's BF16 X (its rounding moves this residual
+by ~4e-5, far inside the 1e-3 tolerance); after timing, the residual of the
+final factors against the FP32 X is computed and compared with the target.
 
-`--impl reference` times the oracle itself.
+Also reported (unless --no-forms):
+- the plain FP32 form (FP32 X, full X.H every sweep, same start and checks),
+  timed to the same target and to its own FP32 target;
+- the FP8 form (E4M3 X with row scales, checks against the FP32 copy);
+- the tensor-core product at widths past the BF16 ridge (N = 256, 512);
+- the batched grouped solver (64 problems x 4 restarts) against the plain FP32
+  solves of all 256, one after another;
+- the learned warm start at reduced size;
+- the end-to-end time through the public API with X copied in from pinned host
+  memory (the `e2e` key);
+- the live rooflines of the dominant kernel (`roofline`) and of the other large
+  one, the SM clocks sampled during the timed region, and the FP64 oracle run
+  on the host cores (`cpu_baseline`).
+
+`--impl reference` times the FP64 oracle itself on the host cores: the same
+solve to the same target with the same checks every 10 sweeps (no
+extrapolation).
 
 Multi-GPU: the method does not shard at these sizes; each rank solves its own
 replica of the workload (independent replicas, weak scaling) and rank 0
@@ -42,6 +55,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -52,8 +66,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N, D, C, K, L, Q, SWEEPS, SEED = 20000, 50, 20, 20, 50, 2, 200, 1
-N_REFINE = 2
+CHECK_EVERY = 10      # LAI sweeps between residual checks
+IR_CHUNK, MAX_IR = 2, 20
+TOL_LOW = 1e-3        # BF16 / FP8 forms: absolute
+TOL_FP32 = 1e-4       # FP32 forms: relative
 METRIC = "time to oracle residual (s) & X·H TFLOP/s|GB/s, mixed/batched/learned vs plain FP32"
+CONFIG = {
+    "workload": "LAI-SymNMF to the FP64 oracle's residual: dense Gaussian-kernel X n=20000 (20-component "
+                "GMM in R^50), k=20, l=50, q=2, residual check every 10 sweeps, target = oracle NR after "
+                "200 plain HALS sweeps + 1e-3",
+    "n": N, "k": K, "l": L, "q": Q, "check_every": CHECK_EVERY, "max_lai_sweeps": SWEEPS,
+    "parallelism": "replicas", "l2": "inputs larger than L2 (BF16 X = 0.8 GB)",
+}
 
 
 def parse():
@@ -64,7 +88,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the FP8 and batched forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP8, tensor, batched and learned forms")
+    ap.add_argument("--forms", default="fp8,tensor,batched,learned",
+                    help="comma-separated subset of the forms to run")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch sweep kernels one by one instead of replaying recorded graphs (for profilers)")
     return ap.parse_args()
@@ -86,6 +112,32 @@ def max_over_ranks(value, world, device):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_threads():
+    """Threads the oracle's BLAS uses (all host cores unless the environment limits them)."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count()
 
 
 # ------------------------------------------------------------------ clocks
@@ -154,12 +206,21 @@ def workload_points():
     return pts, median_pair_distance(pts, seed=0)
 
 
-def golden():
-    path = os.path.join(ROOT, "tests", "golden", "c2_reference.json")
+def golden(name="c2_reference.json"):
+    path = os.path.join(ROOT, "tests", "golden", name)
     if os.path.exists(path):
         with open(path) as f:
             return json.load(f)
     return None
+
+
+def targets():
+    """(target of the BF16 / FP8 forms, target of the FP32 forms, oracle NR) from the stored oracle run."""
+    g = golden()
+    if g is None:
+        raise SystemExit("tests/golden/c2_reference.json is missing (python tests/golden/make_c2_reference.py)")
+    nr = g["plain_nr"]
+    return nr + TOL_LOW, nr * (1.0 + TOL_FP32), nr
 
 
 def peaks():
@@ -193,8 +254,7 @@ def recorded_traffic(name, sources):
         if "=" in line and not line.startswith("#"):
             a, b = line.split("=", 1)
             vals[a.strip()] = b.strip()
-    digest = source_digest(sources)
-    if vals.get("source_sha256_16") != digest:
+    if vals.get("source_sha256_16") != source_digest(sources):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -209,6 +269,41 @@ def fp32_peak_tflops(dev, clk):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+# ------------------------------------------------------- the solve to target
+
+
+def solve_to_target(S, s, target, check_src, lai=True, refine_src=None, max_sweeps=SWEEPS, start=True):
+    """One solve: start, sketch, sweeps in chunks with a residual check after each; stop at the target.
+
+    With lai=False the sweeps use X itself (the plain form).  Returns a dict with the residual of the
+    last check, the sweeps run (LAI or full-X, and refinement) and the number of checks.
+    """
+    if start:
+        s.init_random(True)
+    if lai:
+        s.lai_sketch(L, Q)
+    src = S.SRC_LAI if lai else S.SRC_X
+    done, checks, nr = 0, 0, float("inf")
+    while done < max_sweeps:
+        m = min(CHECK_EVERY, max_sweeps - done)
+        s.sweep(m, source=src, record=False)
+        done += m
+        nr = s.residual(check_src)[0]
+        checks += 1
+        if nr <= target:
+            return {"nr": nr, "sweeps": done, "refine_sweeps": 0, "checks": checks, "reached": True}
+    ir = 0
+    if refine_src is not None:
+        while ir < MAX_IR:
+            s.sweep(IR_CHUNK, source=refine_src, record=False)
+            ir += IR_CHUNK
+            nr = s.residual(check_src)[0]
+            checks += 1
+            if nr <= target:
+                break
+    return {"nr": nr, "sweeps": done, "refine_sweeps": ir, "checks": checks, "reached": nr <= target}
 
 
 def learned_form():
@@ -235,9 +330,10 @@ def learned_form():
     }
 
 
-def batched_form(S, dev, sweeps=100, sample_every=8):
-    """The batched grouped solver on 64 dense SBM problems x 4 restarts (one grouped launch per sweep,
-    graph replay), and the plain FP32 form solving a sample of the same problems one restart at a time."""
+def batched_form(S, dev, sweeps=100):
+    """The batched grouped solver on 64 dense SBM problems x 4 restarts (one grouped launch per half,
+    graph replay), and the plain FP32 form solving all 256 (problem, restart) pairs one at a time."""
+    import numpy as np
     import torch
 
     from synth import batched_problem_specs
@@ -256,7 +352,7 @@ def batched_form(S, dev, sweeps=100, sample_every=8):
         buf = torch.zeros((m, ld), dtype=torch.bfloat16, device=dev)
         buf[:, :m] = A.to(torch.bfloat16)
         Xs.append(buf)
-        Xf.append(A.to(torch.float32) if p % sample_every == 0 else None)
+        Xf.append(A.to(torch.float32))
         del A, P
     b = S.Batch(Xs, [sp["k"] for sp in specs], restarts=4)
     b.init_random(True)
@@ -269,14 +365,22 @@ def batched_form(S, dev, sweeps=100, sample_every=8):
     e1.record()
     torch.cuda.synchronize()
     t_b = e0.elapsed_time(e1) / 1e3
-    b.close()
-    # plain FP32 form: one solver per (problem, restart), full X every sweep, on every `sample_every`-th problem
-    t_p, solves = 0.0, 0
+    info = b.info()
+    # residual of every (problem, restart) after the batched solve, against the FP32 X
+    nr_b = []
     for p, sp in enumerate(specs):
-        if Xf[p] is None:
-            continue
+        H, W = b.factors(p)
+        kc = sp["k"]
         for r in range(4):
-            sv = S.Solver(Xf[p], sp["k"], seed=1 + r)
+            Hr, Wr = H[:, r * kc:(r + 1) * kc], W[:, r * kc:(r + 1) * kc]
+            R = Xf[p] - Wr @ Hr.T
+            nr_b.append(float(torch.linalg.norm(R) / torch.linalg.norm(Xf[p])))
+    b.close()
+    # plain FP32 form: one solver per (problem, restart), full X every sweep, all 256 solves
+    t_p, nr_p = 0.0, []
+    for p, sp in enumerate(specs):
+        for r in range(4):
+            sv = S.Solver(Xf[p], sp["k"], seed=p + r)
             sv.init_random(True)
             sv.sweep(1, record=False)
             torch.cuda.synchronize()
@@ -286,42 +390,54 @@ def batched_form(S, dev, sweeps=100, sample_every=8):
             e1.record()
             torch.cuda.synchronize()
             t_p += e0.elapsed_time(e1) / 1e3
-            solves += 1
+            nr_p.append(sv.residual(S.SRC_X)[0])
             sv.close()
-    scale = (64 * 4) / max(solves, 1)
-    return {"s": t_b, "solves": 256, "sweeps": sweeps, "dtype": "bf16",
-            "plain_fp32_sequential_s": t_p * scale,
-            "plain_sample": f"{solves} of the 256 solves (every {sample_every}th problem, all restarts), "
-                            f"scaled x{scale:.1f}",
-            "speedup_vs_plain": (t_p * scale) / t_b if t_b > 0 else None}
+    out = {"s": t_b, "solves": 256, "sweeps": sweeps, "dtype": "bf16",
+           "plain_fp32_sequential_s": t_p, "plain_solves": len(nr_p),
+           "speedup_vs_plain": t_p / t_b if t_b > 0 else None,
+           "autotuned": info,
+           "nr_batched_mean": float(np.mean(nr_b)), "nr_plain_mean": float(np.mean(nr_p)),
+           "nr_max_abs_diff_vs_plain": float(np.max(np.abs(np.asarray(nr_b) - np.asarray(nr_p))))}
+    gold = golden("c4_reference.json")
+    if gold is not None:
+        ref = np.asarray(gold["nr"])
+        out["nr_max_abs_diff_vs_oracle"] = float(np.max(np.abs(np.asarray(nr_b) - ref)))
+        out["nr_within_1e-3_of_oracle"] = bool(np.all(np.abs(np.asarray(nr_b) - ref) <= 1e-3))
+    return out
 
 
-# --------------------------------------------------------------- oracle side
+def tensor_form(S, dev, Xb, x8, rs8):
+    """The product kernel past the BF16 ridge, timed alone (kernel events) against the measured burst
+    peak of its dtype: N = 256 and N = 512 columns of F over the n = 20000 X."""
+    import torch
 
-
-def oracle_sample(pts, sigma, sweeps_sample=20):
-    """The FP64 oracle on the same instance: sketch + `sweeps_sample` LAI sweeps, scaled to 200 sweeps."""
-    import numpy as np
-
-    from oracle import philox
-    from oracle import symnmf as O
-    from synth import kernel_matrix_numpy
-
-    X = kernel_matrix_numpy(pts, sigma)
-    alpha = O.default_alpha(X)
-    H0 = philox.philox_uniform_factor(N, K, SEED) * O.init_scale(X, K)
-    Om = philox.philox_gaussian(N, L, SEED)
-
-    def one():
-        t0 = time.perf_counter()
-        U, lam = O.apx_evd(X, Om, Q)
-        t1 = time.perf_counter()
-        O.lai_symnmf(U, lam, H0, alpha, sweeps_sample, record=False)
-        t2 = time.perf_counter()
-        return (t1 - t0) + (t2 - t1) * (SWEEPS / sweeps_sample)
-
-    del np
-    return one
+    pk, kind = peaks()
+    out = {}
+    for width in (256, 512):
+        Fw = torch.rand((N, width), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        forms = [("bf16", lambda: S.dense_xf(Xb, Fw, gemm=S.GEMM_TC), pk["bf16_tflops"])]
+        if x8 is not None:
+            forms.append(("fp8", lambda: S.dense_xf(x8, Fw, row_scale=rs8, gemm=S.GEMM_TC),
+                          2.0 * pk["bf16_tflops"]))
+        res = {}
+        for name, fn, peak in forms:
+            try:
+                fn()
+            except S.SymNMFError as e:  # width not built for this dtype
+                res[name] = {"unavailable": str(e)}
+                continue
+            torch.cuda.synchronize()
+            S.profile_standalone(True)
+            for _ in range(10):
+                fn()
+            t_ms, nl, fl, _ = S.profile_standalone_read()
+            S.profile_standalone(False)
+            tf = fl / (t_ms * 1e-3) / 1e12
+            res[name] = {"tflops": tf, "peak_tflops": peak, "frac": tf / peak, "kernel_ms": t_ms / nl,
+                         "peak_kind": f"{kind} burst" if name == "bf16" else f"{kind} BF16 burst x 2 (nominal ratio)"}
+        out[f"N{width}"] = res
+        del Fw
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -341,6 +457,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    tgt_low, tgt_fp32, nr_oracle = targets()
     pts, sigma = workload_points()
     Xf = kernel_matrix_torch(pts, sigma, dev)
     Xb = Xf.to(torch.bfloat16)
@@ -349,11 +466,7 @@ def run_ours(args):
     s = S.Solver(Xb, K, max_width=L, seed=SEED, x_hi=Xf, use_graph=not args.no_graph)
 
     def step():
-        s.init_random(True)
-        s.lai_sketch(L, Q)
-        s.sweep(SWEEPS, source=S.SRC_LAI, record=False)
-        s.sweep(N_REFINE, source=S.SRC_X, record=False)
-        return s.residual(S.SRC_X)[0]
+        return solve_to_target(S, s, tgt_low, S.SRC_X, lai=True, refine_src=S.SRC_X)
 
     for _ in range(args.warmup):
         step()
@@ -372,8 +485,7 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    runs = [step() for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -385,78 +497,55 @@ def run_ours(args):
     clk = clocks.stop()
     ms_step = max_over_ranks(ms_step, world, dev)
 
-    # verification against the oracle's residual (untimed)
+    # verification of the timed solve's result against the FP32 X (untimed)
     nr_true = s.residual(S.SRC_XHI)[0]
-    gold = golden()
-    target = (gold["plain_nr"] + 1e-3) if gold else None
-
+    last = runs[-1]
     out = {}
-    # plain FP32 comparator: same start, FP32 X, full X.H every sweep
+    # plain FP32 comparator: same start, FP32 X, full X.H every sweep, same checks
     if not args.no_plain:
         sp = S.Solver(Xf, K, seed=SEED, use_graph=not args.no_graph)
         sp.init_random(True)
         sp.sweep(1, record=False)
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sp.init_random(True)
-        sp.sweep(SWEEPS, source=S.SRC_X, record=False)
-        nr_plain = sp.residual(S.SRC_X)[0]
-        b.record(stream)
-        torch.cuda.synchronize()
-        out["plain_fp32"] = {"s": a.elapsed_time(b) / 1e3, "nr": nr_plain,
-                             "ok_vs_oracle": (abs(nr_plain - gold["plain_nr"]) <= 1e-4 * gold["plain_nr"])
-                             if gold else None}
+        plain = {}
+        for name, tgt, cap in (("to_mixed_target", tgt_low, SWEEPS), ("to_fp32_target", tgt_fp32, 300)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = solve_to_target(S, sp, tgt, S.SRC_X, lai=False, max_sweeps=cap)
+            b.record(stream)
+            torch.cuda.synchronize()
+            plain[name] = dict(r, s=a.elapsed_time(b) / 1e3, target=tgt)
+        plain["speedup_of_mixed"] = plain["to_mixed_target"]["s"] / (ms_step / 1e3)
+        out["plain_fp32"] = plain
         sp.close()
 
-    if not args.no_forms:
-        # FP8 form of the same solve: X as E4M3 with per-row scales for the sketch and the LAI sweeps,
-        # the FP32 copy for the refinement sweeps
+    forms = set() if args.no_forms else set(args.forms.split(","))
+    x8 = rs8 = None
+    if "fp8" in forms or "tensor" in forms:
         x8, rs8 = S.quantize_fp8(Xf)
+    if "fp8" in forms:
+        # FP8 form: X as E4M3 with per-row scales for the sketch and the sweeps; the checks and any
+        # refinement sweeps use the FP32 copy
         s8 = S.Solver(x8, K, row_scale=rs8, max_width=L, seed=SEED, x_hi=Xf, use_graph=not args.no_graph)
-
-        def step8():
-            s8.init_random(True)
-            s8.lai_sketch(L, Q)
-            s8.sweep(SWEEPS, source=S.SRC_LAI, record=False)
-            s8.sweep(N_REFINE, source=S.SRC_X, record=False)
-            return s8.residual(S.SRC_X)[0]
-
-        step8()
+        solve_to_target(S, s8, tgt_low, S.SRC_XHI, lai=True, refine_src=S.SRC_XHI)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            step8()
+        r8 = [solve_to_target(S, s8, tgt_low, S.SRC_XHI, lai=True, refine_src=S.SRC_XHI)
+              for _ in range(args.steps)]
         b.record(stream)
         torch.cuda.synchronize()
-        out["fp8"] = {"s": a.elapsed_time(b) / 1e3 / args.steps, "nr": s8.residual(S.SRC_XHI)[0],
-                      "reached_target": (s8.residual(S.SRC_XHI)[0] <= target) if target else None}
+        out["fp8"] = dict(r8[-1], s=a.elapsed_time(b) / 1e3 / args.steps, target=tgt_low)
         s8.close()
-        # the product kernel at a width near the BF16 ridge (N = 256: 256 flop per byte of BF16 X,
-        # against a measured ridge of ~279), timed alone (kernel events), against the measured
-        # burst peak of its dtype
-        pk_t, _ = peaks()
-        Fw = torch.rand((N, 256), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
-        tens = {}
-        for name, fn, peak in (("bf16", lambda: S.dense_xf(Xb, Fw, gemm=S.GEMM_TC), pk_t["bf16_tflops"]),
-                               ("fp8", lambda: S.dense_xf(x8, Fw, row_scale=rs8, gemm=S.GEMM_TC),
-                                2.0 * pk_t["bf16_tflops"])):
-            fn()
-            torch.cuda.synchronize()
-            S.profile_standalone(True)
-            for _ in range(10):
-                fn()
-            t_ms, nl, fl, _ = S.profile_standalone_read()
-            S.profile_standalone(False)
-            tf = fl / (t_ms * 1e-3) / 1e12
-            tens[name] = {"tflops": tf, "peak_tflops": peak, "frac": tf / peak, "kernel_ms": t_ms / nl,
-                          "peak_kind": "measured burst" if name == "bf16" else "measured BF16 burst x 2 (nominal ratio)"}
-        out["tensor_n256"] = dict(tens, shape=f"n={N}, N=256 (xf_tc_kernel<256, 256-row tiles>)")
-        del x8, rs8, Fw
+    if "tensor" in forms:
+        out["tensor"] = dict(tensor_form(S, dev, Xb, x8, rs8),
+                             shape=f"n={N} X times F with N = 256 / 512 columns (xf_tc_kernel)")
+    del x8, rs8
+    if "batched" in forms:
         out["batched_c4"] = batched_form(S, dev)
+    if "learned" in forms:
         out["learned_small"] = learned_form()
 
     # end to end through the public API: X from pinned host memory, result back to host
@@ -466,15 +555,11 @@ def run_ours(args):
     def e2e_step():
         Xd = Xh.to(dev, non_blocking=True)
         se = S.Solver(Xd, K, max_width=L, seed=SEED, use_graph=not args.no_graph)
-        se.init_random(True)
-        se.lai_sketch(L, Q)
-        se.sweep(SWEEPS, source=S.SRC_LAI, record=False)
-        se.sweep(N_REFINE, source=S.SRC_X, record=False)
-        nr = se.residual(S.SRC_X)[0]
+        r = solve_to_target(S, se, tgt_low, S.SRC_X, lai=True, refine_src=S.SRC_X)
         H, _ = se.factors()
         Hh = H.cpu()
         se.close()
-        return nr, Hh
+        return r, Hh
 
     e2e_step()
     torch.cuda.synchronize()
@@ -491,33 +576,40 @@ def run_ours(args):
     avg_launch_ms = prod_ms / max(prod_n, 1)
     bytes_per_launch = prod_bytes / max(prod_n, 1)
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if prod_n else None
-    roof_product = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F, N=l=50)", "bound": "hbm", "achieved": achieved,
-                    "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
+    roof_product = {"kernel": "xf_tc_kernel (tcgen05 BF16 X.F: sketch N=l=50, checks N=k=20)", "bound": "hbm",
+                    "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": pk_kind, "unit": "GB/s",
                     "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
                     "traffic": recorded_traffic("xf_tc_bf16_n20000_traffic.txt", PRODUCT_SOURCES),
                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "launches": prod_n,
-                    "tflops": (2.0 * N * N * L / (avg_launch_ms * 1e-3) / 1e12) if prod_n else None}
-    # the dominant kernel of the step: the persistent LAI sweep launch (latency-bound FP32 arithmetic
-    # on shared-memory-resident rows), against the FP32 FMA peak of the part
+                    "share_of_step": (prod_ms / args.steps) / ms_step if prod_n else None}
+    # the persistent LAI sweep launch (latency-bound FP32 arithmetic on shared-memory-resident rows),
+    # against the FP32 FMA peak of the part
     fp32_pk, sms, mhz = fp32_peak_tflops(dev, clk)
     eng_avg_ms = eng_ms / max(eng_n, 1)
     eng_flops_launch = eng_flops / max(eng_n, 1)
     eng_achieved = eng_flops_launch / (eng_avg_ms * 1e-3) / 1e12 if eng_n else None
-    roof = {"kernel": f"lai_resident_kernel (persistent LAI-HALS, {SWEEPS} sweeps per launch, k={K}, l={L})",
-            "bound": "alu", "achieved": eng_achieved, "peak": fp32_pk,
-            "peak_kind": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz", "unit": "TFLOP/s",
-            "frac": (eng_achieved / fp32_pk) if eng_achieved else None,
-            "traffic": recorded_traffic("lai_resident_n20000_k20_l50_traffic.txt", ENGINE_SOURCES),
-            "flops_per_launch": eng_flops_launch, "avg_launch_ms": eng_avg_ms, "launches": eng_n,
-            "share_of_step": (eng_ms / args.steps) / ms_step if eng_n else None}
+    roof_engine = {"kernel": f"lai_resident_kernel (persistent LAI-HALS, {CHECK_EVERY} sweeps per launch, "
+                             f"k={K}, l={L})",
+                   "bound": "alu", "achieved": eng_achieved, "peak": fp32_pk,
+                   "peak_kind": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz", "unit": "TFLOP/s",
+                   "frac": (eng_achieved / fp32_pk) if eng_achieved else None,
+                   "traffic": recorded_traffic("lai_resident_n20000_k20_l50_traffic.txt", ENGINE_SOURCES),
+                   "flops_per_launch": eng_flops_launch, "avg_launch_ms": eng_avg_ms, "launches": eng_n,
+                   "share_of_step": (eng_ms / args.steps) / ms_step if eng_n else None}
+    # the dominant kernel of the step is the `roofline`; the other is reported beside it
+    if (roof_product["share_of_step"] or 0) >= (roof_engine["share_of_step"] or 0):
+        roof, roof_other = roof_product, roof_engine
+    else:
+        roof, roof_other = roof_engine, roof_product
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        one = oracle_sample(pts, sigma)
-        t = one()
-        cpu = {"value": t, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "FP64 oracle on the same instance: Apx-EVD (q=2, l=50) + 20 of the 200 LAI sweeps, "
-                         "sweep time scaled x10; X built in FP64 beforehand (untimed)"}
+        one = oracle_step_fn(pts, sigma, tgt_low)
+        t, r = one()
+        cpu = {"value": t, "unit": "s", "cores": oracle_threads(), "cpu": cpu_model(), "kind": "oracle",
+               "sample": "one full solve of the step by the FP64 oracle on the same instance: Apx-EVD (q=2, l=50) "
+                         "+ LAI-HALS sweeps with a residual check every 10 sweeps to the same target "
+                         f"({r['sweeps']} sweeps, NR {r['nr']:.6f}); X built in FP64 beforehand (untimed)"}
 
     value = ms_step / 1e3
     line = {
@@ -525,16 +617,14 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic (Gaussian-mixture kernel matrix generated on the device)",
-        "config": {"workload": "LAI-SymNMF, dense Gaussian-kernel X n=20000 (20-component GMM in R^50), "
-                               "k=20, l=50, q=2, 200 sweeps + 2 full-X refinement sweeps, X in BF16",
-                   "n": N, "k": K, "l": L, "q": Q, "sweeps": SWEEPS, "refine_sweeps": N_REFINE,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (BF16 X = 0.8 GB)"},
-        "nr_true": nr_true, "nr_target": target, "reached_target": (nr_true <= target) if target else None,
+        "config": dict(CONFIG, parallelism=f"replicas x{world}"),
+        "target": tgt_low, "oracle_nr": nr_oracle,
+        "solve": {"lai_sweeps": last["sweeps"], "refine_sweeps": last["refine_sweeps"], "checks": last["checks"],
+                  "nr_checked": last["nr"], "nr_fp32_x": nr_true, "reached_target": nr_true <= tgt_low},
         "forms": out,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Xh.numel() * 2),
                 "d2h_bytes_per_step": int(N * K * 4)},
-        "roofline": roof, "roofline_product": roof_product, "cpu_baseline": cpu, "clocks": clk,
+        "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(launches),
     }
     if rank == 0:
@@ -544,6 +634,42 @@ def run_ours(args):
     del np
 
 
+# --------------------------------------------------------------- oracle side
+
+
+def oracle_step_fn(pts, sigma, target):
+    """The FP64 oracle's solve of the step: Apx-EVD, LAI-HALS sweeps in chunks of 10, each followed by
+    the true-X residual by the trace trick (a product with X and two k x k Grams), to the target."""
+    import numpy as np
+
+    from oracle import philox
+    from oracle import symnmf as O
+    from synth import kernel_matrix_numpy
+
+    X = kernel_matrix_numpy(pts, sigma)
+    alpha = O.default_alpha(X)
+    normX2 = float((X * X).sum())
+    H0 = philox.philox_uniform_factor(N, K, SEED) * O.init_scale(X, K)
+    Om = philox.philox_gaussian(N, L, SEED)
+
+    def one():
+        t0 = time.perf_counter()
+        U, lam = O.apx_evd(X, Om, Q)
+        W, H = H0.copy(), H0.copy()
+        done, nr = 0, float("inf")
+        while done < SWEEPS:
+            W, H, _ = O.lai_symnmf(U, lam, H, alpha, CHECK_EVERY, W0=W, record=False)
+            done += CHECK_EVERY
+            r2 = O.trace_trick_residual_sq(normX2, W.T @ W, H.T @ H, W.T @ (X @ H))
+            nr = math.sqrt(max(r2, 0.0) / normX2)
+            if nr <= target:
+                break
+        return time.perf_counter() - t0, {"sweeps": done, "nr": nr}
+
+    del np
+    return one
+
+
 # ------------------------------------------------------------- reference arm
 
 
@@ -551,20 +677,25 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    tgt_low, _, _ = targets()
     pts, sigma = workload_points()
-    one = oracle_sample(pts, sigma)
-    for _ in range(args.warmup):
+    one = oracle_step_fn(pts, sigma, tgt_low)
+    # a CPU program has no device state to warm: one warm-up solve whatever W is, so that the whole
+    # run stays within minutes
+    for _ in range(min(args.warmup, 1)):
         one()
-    times = [one() for _ in range(args.steps)]
-    v = sum(times) / len(times)
+    runs = [one() for _ in range(args.steps)]
+    v = sum(t for t, _ in runs) / len(runs)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "LAI-SymNMF, dense Gaussian-kernel X n=20000 (20-component GMM in R^50), "
-                               "k=20, l=50, q=2, 200 sweeps", "n": N, "k": K, "l": L, "q": Q, "sweeps": SWEEPS},
-        "cpu_baseline": {"value": v, "unit": "s", "kind": "oracle", "cores": os.cpu_count(),
-                         "sample": "per step: Apx-EVD + 20 LAI sweeps on the full instance, sweeps scaled x10"},
+        "config": dict(CONFIG, parallelism=f"replicas x{world}"),
+        "solve": runs[-1][1],
+        "cpu_baseline": {"value": v, "unit": "s", "kind": "oracle", "cores": oracle_threads(), "cpu": cpu_model(),
+                         "sample": "each step one full solve by the FP64 oracle (numpy/scipy): Apx-EVD + LAI-HALS "
+                                   "sweeps with a residual check every 10 sweeps to the target; "
+                                   f"{min(args.warmup, 1)} warm-up solve"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

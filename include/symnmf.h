@@ -144,10 +144,18 @@ symnmf_status symnmf_get_factors(symnmf_t h, float* H_out, float* W_out);
 /* Alg. RRF + Alg. Apx-EVD: Y = X Omega, Q = orth(Y), q times
  * { Q = orth(X Q); Q = orth(X Q) }, T = Q^T X Q, T = V Lambda V^T,
  * U = Q V.  orth() is a rank-safe shifted CholeskyQR3 (Fukaya et al. 2020):
- * Grams accumulated in FP64, Cholesky in FP64, pivots below 1e-10 of the
- * largest dropped; the l x l eigen-decomposition is a cyclic Jacobi in FP64.  `omega` (device n x l float32) or NULL for the Philox Gaussian
+ * the Gram Y^T Y from FP32 products folded into Kahan-compensated FP32 sums
+ * and combined in double-float (about 44 significant bits), the Cholesky in
+ * FP64, pivots below 1e-12 (shifted pass) / 1e-10 (plain passes) of the
+ * largest dropped, and the rows solved in FP32; intermediate bases stop after
+ * two passes, the final basis takes three.  T is formed like the Gram; its
+ * eigen-decomposition is a cyclic Jacobi with FP32 rotations, stopped at FP32
+ * rounding (||T - V Lambda V^T||_F <= 8 l 2^-24 ||T||_F), Lambda returned in
+ * FP64.  `omega` (device n x l float32) or NULL for the Philox Gaussian
  * stream (counter (p, i lo, i hi, 1)).  l in [k, max_width], q >= 0.
- * X passes use the problem's X (BF16/FP8 on tensor cores when so stored). */
+ * X passes use the problem's X (BF16/FP8 on tensor cores when so stored).
+ * ||U Lambda U^T||_F^2 (the LAI objective's ||X||^2 term) is formed from
+ * U^T U, so that it matches the stored FP32 U exactly. */
 symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega);
 /* Use a given low-rank approximation X ~ U Lambda U^T instead of a sketch
  * (U device n x l float32 with orthonormal columns, Lambda host double[l]),
@@ -162,15 +170,18 @@ symnmf_status symnmf_get_lai(symnmf_t h, float* U_out, double* lam_out, int* l_o
  * (SYMNMF_SRC_*) and `rule`.  obj_host (host, may be NULL) receives after
  * each sweep the surrogate objective ||X - W H^T||^2 + alpha ||W - H||^2 of
  * that operator, by the trace trick of the "Fast Residual Evaluation"
- * appendix with FP64 accumulation; for SRC_LAI, ||X||^2 is sum(lambda^2).
+ * appendix with FP64 accumulation; for SRC_LAI, ||X||^2 is
+ * ||U Lambda U^T||_F^2 (sum lambda^2 up to the FP32 orthonormality of U).
  * Synchronises only when obj_host != NULL (once, at the end). */
 symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, double* obj_host);
 
 /* ------------------------------------------------------------ LvS (Alg. 2) */
 
 /* Leverage scores of the fixed factor (side 0: H, used to update W; side 1:
- * W) by CholeskyQR: R = chol(F^T F) in FP64, l_i = ||f_i R^{-1}||^2
- * (device double[n] out).  ENOTSPD when F^T F is singular. */
+ * W) by CholeskyQR: F^T F from compensated FP32 sums combined in
+ * double-float, R = chol(F^T F) and R^{-1} in FP64, then l_i = ||f_i R^{-1}||^2
+ * with R^{-1} rounded to FP32 (FP32 row pass; device double[n] out).
+ * ENOTSPD when F^T F is singular (a pivot <= 0). */
 symnmf_status symnmf_leverage(symnmf_t h, int side, double* lev_out);
 
 /* Hybrid sample of the fixed factor for iteration `iter`:
@@ -217,7 +228,10 @@ symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, const float* 
  * float [n x N] with leading dimension N; N <= 128. */
 symnmf_status symnmf_csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                             const float* F, int N, float* Y, void* stream);
-/* G = F^T F in FP64 (device double[N x N]); F device float [n x N]. */
+/* G = F^T F (device double[N x N] out; F device float [n x N], N <= 128):
+ * FP32 products summed over at most 32 rows, folded into Kahan-compensated
+ * FP32 totals, and the block totals combined in double-float in a fixed
+ * order (deterministic; about 44 significant bits). */
 symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G, void* stream);
 /* The same Gram matrix as symnmf_gram, computed without allocating any memory.
  * The paper has no counterpart: this entry point exists for callers that must
@@ -227,11 +241,23 @@ symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G, void* str
  * partials lives in a static device array of 16 MiB (plus one counter) that
  * every GPU that loads this library holds until the process exits.  Limits:
  * N <= 64 (SYMNMF_EINVAL beyond) and at most 256 SMs (SYMNMF_EUNSUPPORTED).
- * The first call on a device looks up the array's device address for that
- * device.  All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.
- * Stream-ordered, no synchronisation. */
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * also loads the library's device symbols there, so make that first call
+ * before any stream capture.  All calls share the array and each leaves its
+ * partials there: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  The result is
+ * bit-identical to symnmf_gram's.  Stream-ordered, no synchronisation. */
 symnmf_status symnmf_gram_noalloc(const float* F, int64_t n, int N, double* G, void* stream);
+/* FP64 Cholesky G + shift I = R^T R (R upper) and R^{-1}, as used for the
+ * leverage scores (Alg. LvS-SymNMF, thin QR of the fixed factor by
+ * CholeskyQR) and, with its pivot-dropping rule, for each CholeskyQR pass of
+ * the range finder.  G device double [k x k] (symmetrised as (G + G^T) / 2),
+ * 1 <= k <= 96, shift >= 0; R and Rinv device double [k x k] row-major, upper
+ * triangular (either may be NULL).  SYMNMF_ENOTSPD when a pivot is not
+ * positive (G + shift I not positive definite); R and Rinv then hold zero rows
+ * for the failed pivots.  Synchronises the stream. */
+symnmf_status symnmf_cholesky(const double* G, int k, double shift, double* R, double* Rinv, void* stream);
 /* Philox Gaussian Omega (device float [n x l]) as in symnmf_lai_sketch. */
 symnmf_status symnmf_gaussian(float* out, int64_t n, int l, uint64_t seed, void* stream);
 /* FP8 copy of a dense float X: row_scale_i = max_j |X_ij| / 448, x8 = e4m3(X / row_scale). */
@@ -265,6 +291,13 @@ symnmf_status symnmf_profile_read_engine(symnmf_t h, double* total_ms, int64_t* 
 /* Number of kernels this library has launched in this process (graph replays
  * count each kernel node). */
 uint64_t symnmf_launch_count(void);
+
+/* Test of the bounded-wait error path: one kernel waits, through the same
+ * bounded wait as the persistent kernels' grid barriers, for a handle word
+ * that nothing sets, gives up after limit_ns (1e3 .. 1e9 ns) and records a
+ * timeout in the handle's device error word; the call then synchronises and
+ * returns SYMNMF_ETIMEOUT.  The handle stays usable (the word is cleared). */
+symnmf_status symnmf_debug_wait_timeout(symnmf_t h, int64_t limit_ns);
 
 /* ------------------------------------------------------------- batched */
 

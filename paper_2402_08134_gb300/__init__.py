@@ -88,10 +88,12 @@ _SIGS = {
     "symnmf_csr_xf": (_I, [_P, _P, _P, _I64, _P, _I, _P, _P]),
     "symnmf_gram": (_I, [_P, _I64, _I, _P, _P]),
     "symnmf_gram_noalloc": (_I, [_P, _I64, _I, _P, _P]),
+    "symnmf_cholesky": (_I, [_P, _I, _D, _P, _P, _P]),
     "symnmf_gaussian": (_I, [_P, _I64, _I, C.c_uint64, _P]),
     "symnmf_quantize_fp8": (_I, [_P, _I64, _I64, _P, _I64, _P, _P]),
     "symnmf_convert_bf16": (_I, [_P, _I64, _I64, _P, _I64, _P]),
     "symnmf_launch_count": (C.c_uint64, []),
+    "symnmf_debug_wait_timeout": (_I, [_P, _I64]),
     "symnmf_profile": (_I, [_P, _I]),
     "symnmf_profile_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
     "symnmf_profile_read_engine": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
@@ -515,6 +517,17 @@ def gram(F, stream=None):
     G = torch.empty((N, N), dtype=torch.float64, device=F.device)
     check(symnmf_gram(_ptr(F), n, N, _ptr(G), _stream(stream)))
     return G
+
+
+def cholesky(G, shift=0.0, stream=None):
+    """(R, R^{-1}) of G + shift I by the library's FP64 block Cholesky (raises ENOTSPD)."""
+    import torch
+
+    k = G.shape[0]
+    R = torch.empty((k, k), dtype=torch.float64, device=G.device)
+    Ri = torch.empty_like(R)
+    check(symnmf_cholesky(_ptr(G), k, float(shift), _ptr(R), _ptr(Ri), _stream(stream)))
+    return R, Ri
 
 
 def gaussian(n, l, seed, stream=None):

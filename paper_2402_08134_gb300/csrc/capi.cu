@@ -12,23 +12,34 @@
 
 #include "../../include/symnmf.h"
 #include "common.cuh"
-#include "kernels.h"
 #include "handle.h"
+#include "kernels.h"
+#include "persist.cuh"
 
 namespace symnmf {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launches(uint64_t n) { g_launches += n; }
 
+// SM count of the current device, looked up once per device (grids and
+// workspaces are sized for the device a call runs on).
 int num_sms() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-    cached = v;
+  constexpr int MAXDEV = 64;
+  static std::atomic<int> cached[MAXDEV];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    dev = 0;
   }
-  return cached;
+  const int slot = dev < MAXDEV ? dev : MAXDEV - 1;
+  int v = dev < MAXDEV ? cached[slot].load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    v = 148;
+  }
+  if (dev < MAXDEV) cached[slot].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 symnmf_status to_status(cudaError_t e) {
@@ -267,6 +278,13 @@ static symnmf_status refresh_grams(symnmf_t h) {
   return SYMNMF_OK;
 }
 
+// One thread waits, through the persistent kernels' bounded wait, for a
+// word that nothing ever sets; the wait runs out after limit_ns and records
+// ERR_TIMEOUT in the handle's error word.
+__global__ void wait_unset_flag_kernel(const unsigned* flag, unsigned* err, uint64_t limit_ns) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) bounded_wait_geq(flag, 1u, err, limit_ns);
+}
+
 // ---------------------------------------------------------------- create
 
 extern "C" symnmf_status symnmf_create(const symnmf_problem* prob, const symnmf_options* opt, void* stream,
@@ -401,6 +419,15 @@ extern "C" symnmf_status symnmf_info(symnmf_t h, double* alpha, double* normX2) 
 
 extern "C" uint64_t symnmf_launch_count(void) { return g_launches.load(); }
 
+extern "C" symnmf_status symnmf_debug_wait_timeout(symnmf_t h, int64_t limit_ns) {
+  if (!h || limit_ns < 1000 || limit_ns > 1000000000) return SYMNMF_EINVAL;
+  // counters[15] is zeroed at create and written by no kernel
+  wait_unset_flag_kernel<<<1, 32, 0, h->st>>>(h->counters + 15, h->err, (uint64_t)limit_ns);
+  count_launches(1);
+  TRY(cudaGetLastError());
+  return check_device_error(h);
+}
+
 // --------------------------------------------------------------- factors
 
 extern "C" symnmf_status symnmf_set_factors(symnmf_t h, const float* H0, const float* W0) {
@@ -478,6 +505,18 @@ static symnmf_status orth(symnmf_t h, float* S, float* T, int l, bool final_basi
   return SYMNMF_OK;
 }
 
+// ||U Lambda U^T||_F^2 of the stored operator, for the trace-trick objective of
+// the LAI sweeps: sum_ij lambda_i lambda_j (U^T U)_ij^2 with U^T U from the
+// compensated cross product.  It equals sum lambda^2 for an exactly
+// orthonormal U; the FP32 U is orthonormal only to rounding, and the
+// objective's other terms use that U, so the norm must too.
+static symnmf_status lai_operator_norm(symnmf_t h, int l) {
+  TRY(xcross(h->U, l, l, h->U, l, l, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
+             h->counters + 0, h->st));
+  TRY(lai_norm2(h->Sm_d, h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  return SYMNMF_OK;
+}
+
 extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega) {
   if (!h) return SYMNMF_EINVAL;
   if (l < h->k || l > h->o.max_width || q < 0) return fail(h, SYMNMF_EINVAL, "need k <= l <= max_width, q >= 0");
@@ -505,7 +544,7 @@ extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float
   TRY(jacobi_evd(h->Sm_d, l, h->V_d, h->lam, h->st));
   TRY(to_float_scaled(h->V_d, l, l, nullptr, h->Sm_f, h->st));
   TRY(apply_small(A, l, l, h->Sm_f, l, n, h->U, l, h->st));
-  TRY(sumsq(h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  TRYS(lai_operator_norm(h, l));
   h->l = l;
   h->lai_ready = true;
   h->lai_version++;
@@ -518,7 +557,7 @@ extern "C" symnmf_status symnmf_set_lai(symnmf_t h, const float* U, const double
   TRYS(ensure_lai(h, l));
   TRY(cudaMemcpyAsync(h->U, U, (size_t)h->n * l * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
   TRY(cudaMemcpyAsync(h->lam, lam_host, (size_t)l * sizeof(double), cudaMemcpyHostToDevice, h->st));
-  TRY(sumsq(h->lam, l, h->scal + S_LAI_NORM2, h->st));
+  TRYS(lai_operator_norm(h, l));
   TRY(cudaStreamSynchronize(h->st));  // lam_host may be released on return
   h->l = l;
   h->lai_ready = true;
@@ -997,13 +1036,34 @@ extern "C" symnmf_status symnmf_gram(const float* F, int64_t n, int N, double* G
   const size_t wsd = xcross_ws_doubles(N, N);
   cudaError_t e;
   if ((e = cudaMallocAsync((void**)&ws, wsd * 8, st)) != cudaSuccess) return to_status(e);
-  if ((e = cudaMallocAsync((void**)&cnt, 4, st)) != cudaSuccess) return to_status(e);
-  cudaMemsetAsync(cnt, 0, 4, st);
+  if ((e = cudaMallocAsync((void**)&cnt, 4, st)) != cudaSuccess) {
+    cudaFreeAsync(ws, st);
+    return to_status(e);
+  }
+  e = cudaMemsetAsync(cnt, 0, 4, st);
   // two blocks per SM, as symnmf_gram_noalloc: both entry points sum in the same order
-  e = xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, cnt, st, 2);
+  if (e == cudaSuccess)
+    e = xcross(F, N, N, F, N, N, n, nullptr, nullptr, nullptr, nullptr, 0.0, G, nullptr, ws, cnt, st, 2);
   cudaFreeAsync(ws, st);
   cudaFreeAsync(cnt, st);
   return to_status(e);
+}
+
+extern "C" symnmf_status symnmf_cholesky(const double* G, int k, double shift, double* R, double* Rinv,
+                                         void* stream) {
+  if (!G || k < 1 || k > 96 || !(shift >= 0.0)) return SYMNMF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&err, sizeof(unsigned), st);
+  if (e != cudaSuccess) return to_status(e);
+  e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = chol_inverse(G, k, shift, 0.0, Rinv, nullptr, err, st, R);
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return to_status(e);
+  return (herr & ERR_NOTSPD) ? SYMNMF_ENOTSPD : SYMNMF_OK;
 }
 
 extern "C" symnmf_status symnmf_gaussian(float* out, int64_t n, int l, uint64_t seed, void* stream) {

@@ -3,10 +3,9 @@
 // Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020).
 // Pass 1 factors Y^T Y + 1e-6 max_i (Y^T Y)_ii I, which is positive definite
 // whatever the rank of Y; passes 2 and 3 are plain CholeskyQR.  Each pass:
-// G = Y^T Y (compensated FP32 partials summed in double-float), G + sI = R^T R
-// in double-float (chol.cuh, dfloat.cuh: GB300's FP64 rate is a small fraction
-// of its FP32 rate), then every row y of Y becomes the solution x of x R = y
-// (forward substitution in FP32).  Pivots below 1e-12 (pass 1) or 1e-10
+// G = Y^T Y (compensated FP32 partials summed in double-float, then taken to
+// FP64), G + sI = R^T R in FP64 (chol.cuh), then every row y of Y becomes the
+// solution x of x R = y (forward substitution in FP32).  Pivots below 1e-12 (pass 1) or 1e-10
 // (passes 2, 3) of the largest diagonal entry are dropped -- a zero column of
 // Q -- so a rank-deficient sketch keeps exactly its numerical range.
 //
@@ -64,14 +63,15 @@ __device__ __forceinline__ void cq_solve_row(float (&s)[LMAX], const float* Rf, 
   }
 }
 
-// R (double-float, upper, in A) -> Rf (FP32 strictly upper, l x l4) and rinv (l4).
-__device__ __forceinline__ void cq_pack_r(const dfl* A, const int* dropped, int l, int l4, float* Rf, float* rinv) {
+// R (FP64, upper, in A) -> Rf (FP32 strictly upper, l x l4) and rinv (l4).
+__device__ __forceinline__ void cq_pack_r(const double* A, const int* dropped, int l, int l4, float* Rf,
+                                          float* rinv) {
   for (int e = threadIdx.x; e < l * l4; e += blockDim.x) {
     const int i = e / l4, j = e - i * l4;
-    Rf[e] = (j > i && j < l) ? A[i * l + j].hi + A[i * l + j].lo : 0.f;
+    Rf[e] = (j > i && j < l) ? (float)A[i * l + j] : 0.f;
   }
   for (int i = threadIdx.x; i < l4; i += blockDim.x)
-    rinv[i] = (i < l && !dropped[i]) ? 1.0f / (A[i * l + i].hi + A[i * l + i].lo) : 0.f;
+    rinv[i] = (i < l && !dropped[i]) ? (float)(1.0 / A[i * l + i]) : 0.f;
 }
 
 __host__ __device__ inline int cq_tiles(int l) {
@@ -107,7 +107,7 @@ constexpr int CQ_BATCH = 16;
 
 __host__ __device__ inline size_t cq_engine_smem(int l, int rp) {
   const int l4 = (l + 3) & ~3;
-  size_t b = (size_t)l * l * 8 + (size_t)2 * l * 8;  // A, piv, 1 / pivot (double-float)
+  size_t b = (size_t)l * l * 8 + (size_t)2 * l * 8;  // A, piv, 1 / pivot (FP64)
   b = (b + 15) & ~(size_t)15;
   b += (size_t)CQ_THREADS * 8;                         // reduction partials (double-float)
   b += (size_t)l4 * (((rp + 7) & ~7) + 32) * 4;       // Yt (skewed columns)
@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
   // column c of Y starts at c P + 4 ((c / 4) mod 8): the 4-column blocks read
   // together by the Gram tiles fall in different bank groups
   auto col = [P](int c) { return c * P + ((c >> 2) & 7) * 4; };
-  dfl* A = reinterpret_cast<dfl*>(smraw);        // l x l
-  dfl* piv = A + l * l;                           // l
-  dfl* invd = piv + l;                            // l
+  double* A = reinterpret_cast<double*>(smraw);  // l x l
+  double* piv = A + l * l;                        // l
+  double* invd = piv + l;                         // l
   dfl* red = reinterpret_cast<dfl*>(smraw + (((size_t)l * l * 8 + (size_t)2 * l * 8 + 15) & ~(size_t)15));
   float* Yt = reinterpret_cast<float*>(red + CQ_THREADS);
   float* Rf = Yt + l4 * P;                        // l x l4
@@ -255,10 +255,10 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
 #pragma unroll 4
     for (int e = tid; e < E; e += CQ_THREADS) {
       const float2 f = __ldcg(reinterpret_cast<const float2*>(a.fin + e));
-      A[e] = dfl{f.x, f.y};
+      A[e] = (double)f.x + (double)f.y;
     }
     __syncthreads();
-    chol_upper_block_df(A, l, cq_shift(pass), cq_drop(pass), piv, invd, dropped, tri);
+    chol_upper_block(A, l, cq_shift(pass), cq_drop(pass), piv, invd, dropped, tri, nullptr);
     cq_pack_r(A, dropped, l, l4, Rf, rinv);
     __syncthreads();
     for (int r = tid; r < R; r += CQ_THREADS) {
@@ -284,16 +284,16 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) cholqr_engine_kernel(CqArgs a) 
 // ------------------------------------------------------ multi-kernel passes
 
 __global__ void chol_factor_kernel(const double* G, int l, double shift, double drop_tol, float* Rf, float* rinv) {
-  extern __shared__ __align__(16) dfl Ash[];  // l x l, then the triangle entries
-  __shared__ dfl piv[128], invd[128];
+  extern __shared__ __align__(16) double Ash[];  // l x l, then the triangle entries
+  __shared__ double piv[128], invd[128];
   __shared__ int dropped[128];
   const int l4 = (l + 3) & ~3;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e - i * l;
-    Ash[e] = df_from_double(0.5 * (G[i * l + j] + G[j * l + i]));
+    Ash[e] = 0.5 * (G[i * l + j] + G[j * l + i]);
   }
   __syncthreads();
-  chol_upper_block_df(Ash, l, shift, drop_tol, piv, invd, dropped, reinterpret_cast<ushort2*>(Ash + l * l));
+  chol_upper_block(Ash, l, shift, drop_tol, piv, invd, dropped, reinterpret_cast<ushort2*>(Ash + l * l), nullptr);
   cq_pack_r(Ash, dropped, l, l4, Rf, rinv);
 }
 

@@ -87,6 +87,8 @@ cudaError_t objective(const double* normX2, const double* Ga, const double* Gb, 
 cudaError_t pair_reduce(const float* a, const float* b, int64_t count, double* out, double* ws,
                         unsigned* counter, cudaStream_t st);
 cudaError_t sumsq(const double* v, int l, double* out, cudaStream_t st);
+// out = ||U diag(lam) U^T||_F^2 = sum_ij lam_i lam_j Gu_ij^2 with Gu = U^T U (l x l FP64).
+cudaError_t lai_norm2(const double* Gu, const double* lam, int l, double* out, cudaStream_t st);
 
 // Projected gradient partial: sum over entries of (grad)^2 where grad < 0 or F > 0,
 // grad = 2 (F Gother - Y) + 2 alpha (F - Other).  Adds into acc[0] (FP64 atomics).
@@ -107,12 +109,12 @@ cudaError_t check_factor(const float* F, int64_t count, unsigned* flags, cudaStr
 cudaError_t normalize_rows(const float* in, int64_t n, int l, float* out, cudaStream_t st);
 
 // --------------------------------------------------------- small dense
-// Cholesky of G + shift I (k <= 96) in double-float: R upper, Rinv (FP64 and
-// FP32 copies).
+// Cholesky of G + shift I (k <= 96) in FP64: R upper (optional FP64 copy in
+// R), Rinv (FP64 and FP32 copies, each optional).
 // drop_tol > 0: pivots <= drop_tol * max_diag give zero rows/cols in Rinv
 // (rank-safe mode); else such a pivot sets ERR_NOTSPD.
 cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,
-                         float* Rinv_f, unsigned* err, cudaStream_t st);
+                         float* Rinv_f, unsigned* err, cudaStream_t st, double* R = nullptr);
 // Symmetric Jacobi eigen-decomposition of A (l <= 128): V (columns = vectors), lam.
 cudaError_t jacobi_evd(const double* A, int l, double* V, double* lam, cudaStream_t st);
 // B = V diag(lam_j^{-1/2}) for lam_j > tol * max(lam) else 0 (FP32 out, l x l).

@@ -620,6 +620,27 @@ cudaError_t sumsq(const double* v, int l, double* out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ||U diag(lam) U^T||_F^2 = sum_ij lam_i lam_j (U^T U)_ij^2 from the Gram Gu =
+// U^T U (l x l, FP64), summed in FP64 in a fixed order: the exact norm of the
+// operator the LAI sweeps apply, whose U is orthonormal only to FP32 rounding.
+__global__ void lai_norm2_kernel(const double* Gu, const double* lam, int l, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e - i * l;
+    const double g = Gu[e];
+    s += lam[i] * lam[j] * g * g;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+cudaError_t lai_norm2(const double* Gu, const double* lam, int l, double* out, cudaStream_t st) {
+  lai_norm2_kernel<<<1, 256, 0, st>>>(Gu, lam, l, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- projected gradient
 
 __global__ void proj_grad_kernel(const float* __restrict__ F, const float* __restrict__ O,

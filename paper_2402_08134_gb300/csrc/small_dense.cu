@@ -1,75 +1,71 @@
-// Single-CTA FP64 kernels on k x k / l x l matrices: Cholesky with explicit
-// triangular inverse (CholeskyQR of the LvS section, second CholeskyQR2 pass
-// of the range finder) and cyclic Jacobi eigen-decomposition (Alg. Apx-EVD,
-// T = Q_T Lambda Q_T^T, and the rank-safe first orthonormalisation pass).
+// Single-CTA kernels on k x k / l x l matrices: FP64 Cholesky with explicit
+// triangular inverse (the leverage scores' CholeskyQR of the LvS section) and
+// cyclic Jacobi eigen-decomposition (Alg. Apx-EVD, T = Q_T Lambda Q_T^T).
 #include <math.h>
 
 #include <algorithm>
 
 #include "common.cuh"
 #include "chol.cuh"
-#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace symnmf {
 
-constexpr int CI_KMAX = 96;  // chol_inverse: 2 k^2 double-float pairs of shared memory
+constexpr int CI_KMAX = 96;  // chol_inverse: 2 k^2 doubles of shared memory
 
-// A = G + shift I = R^T R (R upper), then Rinv = R^{-1}, both in double-float
-// (pairs of FP32, Dekker's error-free transformations; chol.cuh): FP64 runs
-// at ~1/64 of the FP32 rate on this part.  The Cholesky is
-// chol_upper_block_df; the inverse goes row by row from the bottom,
+// A = G + shift I = R^T R (R upper), then Rinv = R^{-1}, both in FP64.  The
+// Cholesky is chol_upper_block (chol.cuh); the inverse goes row by row from
+// the bottom,
 //   Rinv[i][c] = -(sum_{i < j <= c} R[i][j] Rinv[j][c]) / R[i][i],
 // each row's entries in parallel, TPC threads per entry (a shuffle tree).  A
 // dropped pivot gives a zero row/column of Rinv; in strict mode
 // (drop_tol <= 0) it also raises ERR_NOTSPD.
 __global__ void chol_inverse_kernel(const double* G, int k, double shift, double drop_tol, double* Rinv,
-                                    float* Rinv_f, unsigned* err) {
+                                    float* Rinv_f, unsigned* err, double* Rout) {
   extern __shared__ __align__(16) unsigned char ci_raw[];
-  dfl* A = reinterpret_cast<dfl*>(ci_raw);  // k x k, becomes R
-  dfl* X = A + k * k;                       // k x k, becomes R^{-1}
+  double* A = reinterpret_cast<double*>(ci_raw);  // k x k, becomes R
+  double* X = A + k * k;                          // k x k, becomes R^{-1}
   ushort2* tri = reinterpret_cast<ushort2*>(X + k * k);
-  __shared__ dfl piv[CI_KMAX], invd[CI_KMAX];
+  __shared__ double piv[CI_KMAX], invd[CI_KMAX];
   __shared__ int dropped[CI_KMAX];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    A[e] = df_from_double(0.5 * (G[i * k + j] + G[j * k + i]));
-    X[e] = dfl{0.f, 0.f};
+    A[e] = 0.5 * (G[i * k + j] + G[j * k + i]);
+    X[e] = 0.0;
   }
   __syncthreads();
-  chol_upper_block_df(A, k, shift, drop_tol, piv, invd, dropped, tri);
-  if (drop_tol <= 0.0 && tid < k && dropped[tid]) set_error(err, ERR_NOTSPD);
+  chol_upper_block(A, k, shift, drop_tol, piv, invd, dropped, tri, err);
   const int tpc = k <= nt / 8 ? 8 : k <= nt / 4 ? 4 : k <= nt / 2 ? 2 : 1;  // threads per entry
   const int c = tid / tpc, part = tid - c * tpc;
   for (int i = k - 1; i >= 0; --i) {
-    const dfl rii = A[i * k + i];
-    const dfl rinv = rii.hi > 0.f ? df_rsqrt(df_mul(rii, rii)) : dfl{0.f, 0.f};
-    dfl acc{0.f, 0.f};
+    // 1 / R_ii = sqrt(1 / pivot) = piv[i] (0 for a dropped pivot)
+    const double rinv = dropped[i] ? 0.0 : piv[i];
+    double acc = 0.0;
     if (c < k && c > i)
-      for (int j = i + 1 + part; j <= c; j += tpc) acc = df_fms(acc, A[i * k + j], X[j * k + c]);
-    for (int o = 1; o < tpc; o <<= 1)
-      acc = df_add(acc, dfl{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
-    if (part == 0 && c < k && c >= i) X[i * k + c] = c == i ? rinv : df_mul(acc, rinv);
+      for (int j = i + 1 + part; j <= c; j += tpc) acc = fma(-A[i * k + j], X[j * k + c], acc);
+    for (int o = 1; o < tpc; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (part == 0 && c < k && c >= i) X[i * k + c] = c == i ? rinv : acc * rinv;
     __syncthreads();
   }
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    const double v = (j >= i) ? df_to_double(X[e]) : 0.0;
+    const double v = (j >= i) ? X[e] : 0.0;
     if (Rinv) Rinv[e] = v;
     if (Rinv_f) Rinv_f[e] = (float)v;
+    if (Rout) Rout[e] = A[e];
   }
 }
 
 cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, double* Rinv,
-                         float* Rinv_f, unsigned* err, cudaStream_t st) {
+                         float* Rinv_f, unsigned* err, cudaStream_t st, double* R) {
   if (k < 1 || k > CI_KMAX) return cudaErrorInvalidValue;
-  // two k x k double-float matrices and the triangle's index table
-  const size_t smem = (size_t)2 * k * k * sizeof(dfl) + (size_t)k * (k + 1) / 2 * sizeof(ushort2);
+  // two k x k FP64 matrices and the triangle's index table
+  const size_t smem = (size_t)2 * k * k * sizeof(double) + (size_t)k * (k + 1) / 2 * sizeof(ushort2);
   cudaError_t e = cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  chol_inverse_kernel<<<1, 256, smem, st>>>(G, k, shift, drop_tol, Rinv, Rinv_f, err);
+  chol_inverse_kernel<<<1, 256, smem, st>>>(G, k, shift, drop_tol, Rinv, Rinv_f, err, R);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -66,3 +66,53 @@ def test_reference_arm_runs_on_rank_zero_only():
                        env=env, capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+class _FakeLib:
+    SRC_X, SRC_LAI, SRC_XHI = 0, 1, 2
+
+
+class _FakeSolver:
+    """Residual falls by a fixed factor per sweep; records what the driver asked for."""
+
+    def __init__(self, nr0, rate):
+        self.nr, self.rate, self.log = nr0, rate, []
+
+    def init_random(self, scaled):
+        self.log.append(("init", scaled))
+
+    def lai_sketch(self, l, q):
+        self.log.append(("sketch", l, q))
+
+    def sweep(self, m, source, record):
+        self.log.append(("sweep", m, source))
+        self.nr *= self.rate ** m
+
+    def residual(self, src):
+        self.log.append(("check", src))
+        return self.nr, 0.0
+
+
+def test_solve_to_target_stops_at_the_first_check_below_target():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s = _FakeSolver(1.0, 0.9)
+    r = bench.solve_to_target(_FakeLib, s, 0.9 ** 35, _FakeLib.SRC_X, lai=True, refine_src=_FakeLib.SRC_X)
+    # checks after 10, 20, 30, 40 LAI sweeps; 0.9^40 is the first at or below 0.9^35
+    assert r["reached"] and r["sweeps"] == 40 and r["checks"] == 4 and r["refine_sweeps"] == 0
+    assert s.log[:2] == [("init", True), ("sketch", bench.L, bench.Q)]
+    assert all(e[2] == _FakeLib.SRC_LAI for e in s.log if e[0] == "sweep")
+
+
+def test_solve_to_target_refines_with_full_x_when_lai_stalls():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s = _FakeSolver(1.0, 1.0)  # the LAI sweeps make no progress
+    r = bench.solve_to_target(_FakeLib, s, 0.5, _FakeLib.SRC_X, lai=True, refine_src=_FakeLib.SRC_X)
+    assert r["sweeps"] == bench.SWEEPS and not r["reached"]
+    assert r["refine_sweeps"] == bench.MAX_IR
+    assert r["checks"] == bench.SWEEPS // bench.CHECK_EVERY + bench.MAX_IR // bench.IR_CHUNK
+    refine = [e for e in s.log if e[0] == "sweep" and e[2] == _FakeLib.SRC_X]
+    assert len(refine) == bench.MAX_IR // bench.IR_CHUNK

@@ -8,6 +8,7 @@ from oracle import philox
 from oracle import symnmf as O
 from synth import planted_dense, uniform_factor
 
+from ._fp32_hals import hals_fp32
 from ._gpu_util import np64, rel_err, t32, t64
 
 pytestmark = pytest.mark.gpu
@@ -35,24 +36,36 @@ def test_planted_fp64_hals_100_sweeps(S, use_graph):
     assert (np.diff(got) <= 1e-7 * nx2).all()
 
 
-def test_planted_fp32_hals_and_residual(S):
-    # the planted configuration (seed 0) with X in FP32.  Some other seeds show a transient
-    # ~1e-4 deviation under any FP32 arithmetic (a plain float32 numpy HALS reaches 1.04e-4
-    # at sweep 10 on seed 1): trajectory sensitivity, not kernel error
-    X, Hi, labels = _planted(n=1000, k=10, seed=0)
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_planted_fp32_hals_and_residual(S, seed):
+    # the planted configuration with X in FP32, seeds 0-3.  Any float32 arithmetic drifts from
+    # the FP64 oracle along the way (a float32 numpy restatement of the same sweeps,
+    # tests/_fp32_hals.py, deviates up to 1.0e-4 on seed 0 and 5.7e-4 on seed 3, transiently
+    # around sweep 10): the GPU trajectory must stay within 1e-4 of the oracle or within three
+    # times that float32 drift, and end within 1e-4
+    X, Hi, labels = _planted(n=1000, k=10, seed=seed)
     s = S.Solver(t32(X), 10)
     s.set_factors(t32(Hi))
-    got = s.sweep(60)
+    got = np.asarray(s.sweep(60))
     alpha = O.default_alpha(X)
-    W, H, ref = O.hals_symnmf(X, Hi.astype(np.float32).astype(np.float64), alpha, 60)
-    assert rel_err(got, ref).max() < 1e-4
+    Hi32 = Hi.astype(np.float32).astype(np.float64)
+    W, H, ref = O.hals_symnmf(X, Hi32, alpha, 60)
+    ref = np.asarray(ref)
+    W32, H32, o32 = hals_fp32(X, Hi32, alpha, 60)
+    drift = np.abs(np.asarray(o32) - ref) / ref
+    dev = rel_err(got, ref)
+    assert dev.max() <= max(1e-4, 3.0 * drift.max()), (dev.max(), drift.max())
+    assert dev[-1] < 1e-4
     nr, obj, pg = s.residual(S.SRC_X, proj_grad=True)
     Hg, Wg = s.factors()
     Hg, Wg = np64(Hg), np64(Wg)
     assert nr == pytest.approx(O.normalized_residual(X, Wg, Hg), rel=1e-4)
     assert obj == pytest.approx(O.surrogate_objective(X, Wg, Hg, alpha), rel=1e-4)
     assert pg == pytest.approx(O.projected_gradient_norm(X, Wg, Hg, alpha), rel=1e-3, abs=1e-6)
-    np.testing.assert_allclose(Hg, H, rtol=1e-2, atol=1e-4)
+    # factors element by element: within five times the float32 restatement's distance
+    tol = max(5.0 * max(np.abs(H32 - H).max(), np.abs(W32 - W).max()), 2e-6)
+    np.testing.assert_allclose(Hg, H, rtol=0, atol=tol)
+    np.testing.assert_allclose(Wg, W, rtol=0, atol=tol)
 
 
 def test_bpp_rule_matches_oracle(S):
