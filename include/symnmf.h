@@ -72,7 +72,13 @@ typedef enum {
 enum {
   SYMNMF_SRC_X = 0,   /* the problem's X in its own format */
   SYMNMF_SRC_LAI = 1, /* U Lambda U^T from symnmf_lai_sketch (Alg. LAI-SymNMF) */
-  SYMNMF_SRC_XHI = 2  /* the optional float32 copy x_hi (correction / refinement sweeps) */
+  SYMNMF_SRC_XHI = 2, /* the optional float32 copy x_hi (correction / refinement sweeps) */
+  SYMNMF_SRC_COMP = 3 /* Compressed-NMF (appendix "Comparison between LAI-NMF and
+                         Compressed-NMF"): each half solves the compressed problem
+                         min ||Q^T (F_fix F^T - X)||^2 + alpha ||F - F_fix||^2 on the
+                         last sketch's basis Q, i.e. Update(G_c + alpha I, Y_c + alpha
+                         F_fix) with M = Q^T F_fix, G_c = M^T M, Y_c = (X Q) M; sweeps
+                         only (not a residual or PGNCG source) */
 };
 
 /* Update rule: Update(G, Y) of the paper's appendix. */
@@ -120,8 +126,9 @@ typedef struct {
 
 /* Create a solver for one problem.  Validates sizes and alignment (EINVAL),
  * allocates W, H and workspaces (ENOMEM), computes ||X||_F^2 and, when
- * prob->alpha <= 0, alpha = max_ij X_ij on `stream`.  W and H start at zero:
- * call symnmf_set_factors or symnmf_init_random before sweeping. */
+ * prob->alpha <= 0, alpha = max_ij X_ij on `stream` (ENAN when X or x_hi
+ * holds a non-finite entry).  W and H start at zero: call symnmf_set_factors
+ * or symnmf_init_random before sweeping. */
 symnmf_status symnmf_create(const symnmf_problem* prob, const symnmf_options* opt, void* stream,
                             symnmf_t* out);
 void symnmf_destroy(symnmf_t h);
@@ -157,6 +164,17 @@ symnmf_status symnmf_get_factors(symnmf_t h, float* H_out, float* W_out);
  * ||U Lambda U^T||_F^2 (the LAI objective's ||X||^2 term) is formed from
  * U^T U, so that it matches the stored FP32 U exactly. */
 symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega);
+/* The same sketch with the basis from the adaptive range finder (appendix,
+ * Alg. Ada-RRF): Q = orth(X Omega); then at most q_max times: B^T = X Q,
+ * residual r = sqrt(||X||^2 - ||B||^2) / ||X|| (the appendix's QB identity,
+ * ||B||^2 summed in FP64), Q = orth(B^T); stop when r fell by less than `tol`
+ * since the previous check (the experiments use 1e-3); otherwise Q =
+ * orth(X Q).  Then T = Q^T X Q and U, Lambda as in symnmf_lai_sketch.  Host
+ * outputs (each may be NULL): checks_out = number of residual checks,
+ * passes_out = products with X including the one for T, nr_hist[checks] =
+ * the residuals (room for q_max values).  Synchronises once per check. */
+symnmf_status symnmf_lai_sketch_ada(symnmf_t h, int l, int q_max, double tol, const float* omega,
+                                    int* checks_out, int* passes_out, double* nr_hist);
 /* Use a given low-rank approximation X ~ U Lambda U^T instead of a sketch
  * (U device n x l float32 with orthonormal columns, Lambda host double[l]),
  * e.g. a truncated EVD computed elsewhere.  Copies both; synchronises. */
@@ -171,9 +189,25 @@ symnmf_status symnmf_get_lai(symnmf_t h, float* U_out, double* lam_out, int* l_o
  * each sweep the surrogate objective ||X - W H^T||^2 + alpha ||W - H||^2 of
  * that operator, by the trace trick of the "Fast Residual Evaluation"
  * appendix with FP64 accumulation; for SRC_LAI, ||X||^2 is
- * ||U Lambda U^T||_F^2 (sum lambda^2 up to the FP32 orthonormality of U).
- * Synchronises only when obj_host != NULL (once, at the end). */
+ * ||U Lambda U^T||_F^2 (sum lambda^2 up to the FP32 orthonormality of U);
+ * for SRC_COMP the value is the H half's compressed objective
+ * ||Q^T (W H^T - X)||^2 + alpha ||W - H||^2.
+ * Synchronises only when obj_host != NULL (once, at the end); a non-finite
+ * recorded objective returns SYMNMF_ENAN. */
 symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, double* obj_host);
+
+/* `iters` iterations of PGNCG-SymNMF on the SymNMF objective ||X - H H^T||_F^2
+ * (section "Projected Gauss-Newton with Conjugate Gradients for SymNMF";
+ * with source = SYMNMF_SRC_LAI the appendix's LAI-PGNCG-SymNMF, X H replaced
+ * by U (Lambda (U^T H))).  Per iteration: R = 2 (H H^T H - X H); s_max steps
+ * of conjugate gradients on the Gauss-Newton normal equations
+ * 2 (Z H^T H + H Z^T H) = R from Z = 0 (stopped early once ||R|| falls
+ * below 1e-6 of its start); H = max(H - Z, 0).  Row work in FP32, CG
+ * scalars and reductions in FP64, all on the device.  W follows H (W := H).
+ * obj_host (host, may be NULL): ||X - H H^T||_F^2 after each iteration, by the
+ * trace trick with FP64 accumulation (one extra product with X in all);
+ * synchronises only then.  iters <= 4096, 1 <= s_max <= 1000. */
+symnmf_status symnmf_pgncg(symnmf_t h, int iters, int source, int s_max, double* obj_host);
 
 /* ------------------------------------------------------------ LvS (Alg. 2) */
 
@@ -200,7 +234,8 @@ symnmf_status symnmf_lvs_sample(symnmf_t h, int side, int iter, double tau, int 
                                 double* theta);
 /* Update W (side 0) or H (side 1) from the stored sample: Y = X S^T S F,
  * G = F^T S^T S F, then Update(G + alpha I, Y + alpha F) by `rule`.  X must
- * be CSR (sampled columns = sampled rows by symmetry) or dense F32/F64. */
+ * be CSR or dense F64/F32/BF16: the sampled columns of X are read as the
+ * sampled rows (X is symmetric), contiguous in memory. */
 symnmf_status symnmf_lvs_update(symnmf_t h, int side, int rule);
 /* `iters` full LvS iterations entirely on the device (leverage, sample,
  * sampled products, update; both halves), counters iter0 .. iter0+iters-1.

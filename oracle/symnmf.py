@@ -188,6 +188,46 @@ def apx_evd(X, Omega, q):
     return Q @ QT, lam
 
 
+def ada_rrf(X, Omega, q_max, tol=1e-3):
+    """Adaptive randomised range finder (appendix, Alg. Ada-RRF), X symmetric so X^T = X.
+
+    Q = qr(X Omega); then at most q_max times: B^T = X^T Q, the QB residual
+    ||Q B - X||_F^2 = ||X||_F^2 - ||B||_F^2 (the appendix's identity) gives the
+    normalized residual r_j = sqrt(||X||^2 - ||B||^2) / ||X||, Q = qr(B^T);
+    stop when the residual fell by less than `tol` since the previous check
+    (the experiments' rule: 1e-3 per power iteration); otherwise Y = X Q,
+    Q = qr(Y).  Householder thin QR stands for qr().
+
+    Returns (Q, hist, passes): the residuals r_1, r_2, ... of the checks made,
+    and the number of products with X.
+    """
+    normX2 = float((X * X).sum())
+    Q, _ = np.linalg.qr(X @ Omega)
+    passes, hist = 1, []
+    for _ in range(q_max):
+        Bt = X.T @ Q
+        passes += 1
+        hist.append(math.sqrt(max(normX2 - float((Bt * Bt).sum()), 0.0) / normX2))
+        Q, _ = np.linalg.qr(Bt)
+        if len(hist) >= 2 and hist[-2] - hist[-1] < tol:
+            break
+        Q, _ = np.linalg.qr(X @ Q)
+        passes += 1
+    return Q, hist, passes
+
+
+def apx_evd_ada(X, Omega, q_max, tol=1e-3):
+    """Alg. Apx-EVD with the basis from Alg. Ada-RRF: T = Q^T X Q = V Lambda V^T, U = Q V.
+
+    Returns (U, lam, hist, passes); passes counts the product for T as well.
+    """
+    Q, hist, passes = ada_rrf(X, Omega, q_max, tol)
+    T = Q.T @ (X @ Q)
+    T = 0.5 * (T + T.T)
+    lam, V = np.linalg.eigh(T)
+    return Q @ V, lam, hist, passes + 1
+
+
 def lai_product(U, lam, F):
     """X F replaced by U (Lambda (U^T F)) (Alg. LAI-SymNMF, Y_H and Y_W lines)."""
     return U @ (lam[:, None] * (U.T @ F))
@@ -239,6 +279,101 @@ def lai_symnmf(U, lam, H0, alpha, sweeps, W0=None, rule="hals", record=True):
             r2 = trace_trick_residual_sq(normX2, W.T @ W, H.T @ H, H.T @ Y)
             objs.append(r2 + alpha * float(((W - H) ** 2).sum()))
     return W, H, objs
+
+
+# ------------------------------------------------------------- Compressed-NMF
+
+
+def compressed_half(Xt_Q, Q, Fold, Ffix, alpha, rule="hals"):
+    """One half of Compressed-SymNMF (appendix "Comparison between LAI-NMF and Compressed-NMF"):
+    min_{F >= 0} ||Q^T (Ffix F^T - X)||_F^2 + alpha ||F - Ffix||_F^2, Q = RRF(X) (one basis, X symmetric).
+
+    Its normal equations give Update(G_c + alpha I, Y_c + alpha Ffix) with M = Q^T Ffix (l x k),
+    G_c = M^T M = Ffix^T Q Q^T Ffix and Y_c = X^T Q M (Xt_Q = X^T Q, computed once).
+    """
+    M = Q.T @ Ffix
+    G = M.T @ M
+    Y = Xt_Q @ M
+    if rule == "hals":
+        return hals_update_efficient(Fold, Ffix, G, Y, alpha), G, Y
+    return bpp_update(Ffix, G, Y, alpha), G, Y
+
+
+def compressed_symnmf(X, Q, H0, alpha, sweeps, W0=None, rule="hals"):
+    """Compressed-SymNMF sweeps (W half then H half).  Returns (W, H, objs): objs[t] is the H half's
+    compressed objective ||Q^T (W H^T - X)||_F^2 + alpha ||W - H||_F^2 after sweep t."""
+    H = np.array(H0, dtype=np.float64, copy=True)
+    W = H.copy() if W0 is None else np.array(W0, dtype=np.float64, copy=True)
+    Xt_Q = X.T @ Q
+    B = Q.T @ X
+    objs = []
+    for _ in range(sweeps):
+        W, _, _ = compressed_half(Xt_Q, Q, W, H, alpha, rule)
+        H, _, _ = compressed_half(Xt_Q, Q, H, W, alpha, rule)
+        R = (Q.T @ W) @ H.T - B
+        objs.append(float((R * R).sum() + alpha * ((W - H) ** 2).sum()))
+    return W, H, objs
+
+
+# ------------------------------------------------------------- PGNCG (all-at-once)
+
+
+def gn_jacobian_apply(H, P):
+    """J p for the residual r(H) = vec(H H^T - X): d/dt (H + t P)(H + t P)^T at t = 0 = P H^T + H P^T."""
+    return P @ H.T + H @ P.T
+
+
+def gn_normal_apply(H, G, P):
+    """J^T J p = 2 (P H^T H + H P^T H) (section "Projected Gauss-Newton with Conjugate Gradients"),
+    with G = H^T H; J^T applied to a symmetric n x n residual S is 2 S H."""
+    return 2.0 * (P @ G + H @ (P.T @ H))
+
+
+def pgncg_iteration(Y, H, s_max):
+    """One PGNCG iteration (section "Projected Gauss-Newton with Conjugate Gradients", appendix
+    Alg. LAI-PGNCG-SymNMF) given Y = X H (or U Lambda U^T H for LAI-PGNCG).
+
+    R = J^T r = 2 (H (H^T H) - X H), the Gauss-Newton normal equations J^T J Z = R solved from
+    Z = 0 by s_max steps of conjugate gradients, then H <- max(H - Z, 0).  The printed loop never
+    updates the search direction and reuses alpha; this restatement takes standard CG (step
+    alpha = e_old / <P, J^T J P>, beta = e_new / e_old, P <- R + beta P), stopped early once CG
+    has converged (||R|| <= 1e-12 ||R_0||): past that point the recurrence divides rounding noise.
+    """
+    G = H.T @ H
+    R = 2.0 * (H @ G - Y)
+    P = R.copy()
+    Z = np.zeros_like(H)
+    e_old = float((R * R).sum())
+    e_stop = 1e-24 * e_old
+    for _ in range(s_max):
+        if e_old <= e_stop or e_old == 0.0:
+            break
+        Yc = gn_normal_apply(H, G, P)
+        a = e_old / float((P * Yc).sum())
+        Z += a * P
+        R -= a * Yc
+        e_new = float((R * R).sum())
+        P = R + (e_new / e_old) * P
+        e_old = e_new
+    return np.maximum(H - Z, 0.0)
+
+
+def symnmf_objective(normX2, HtH, HtXH):
+    """||X - H H^T||_F^2 = ||X||^2 - 2 tr(H^T X H) + ||H^T H||_F^2 (trace trick, Eq. symnmf_obj)."""
+    return float(normX2 - 2.0 * np.trace(HtXH) + (HtH * HtH).sum())
+
+
+def pgncg_symnmf(apply_x, normX2, H0, iters, s_max=5):
+    """PGNCG-SymNMF (apply_x = X @) or LAI-PGNCG-SymNMF (apply_x = U Lambda U^T @).
+
+    Returns (H, objs): objs[t] = ||X - H H^T||_F^2 after iteration t, with ||X||^2 = normX2.
+    """
+    H = np.array(H0, dtype=np.float64, copy=True)
+    objs = []
+    for _ in range(iters):
+        H = pgncg_iteration(apply_x(H), H, s_max)
+        objs.append(symnmf_objective(normX2, H.T @ H, H.T @ apply_x(H)))
+    return H, objs
 
 
 # ------------------------------------------------------------ leverage scores

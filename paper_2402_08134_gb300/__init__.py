@@ -30,7 +30,7 @@ _lib = C.CDLL(LIB_PATH)
 # ---------------------------------------------------------------- constants
 OK, EINVAL, ENOMEM, ENOTSPD, ETIMEOUT, ENAN, ECUDA, ESTATE, EUNSUPPORTED = range(9)
 X_DENSE_F64, X_DENSE_F32, X_DENSE_BF16, X_DENSE_FP8, X_CSR_F32 = range(5)
-SRC_X, SRC_LAI, SRC_XHI = range(3)
+SRC_X, SRC_LAI, SRC_XHI, SRC_COMP = range(4)
 RULE_HALS, RULE_BPP = range(2)
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = range(3)
 
@@ -75,9 +75,11 @@ _SIGS = {
     "symnmf_init_random": (_I, [_P, _I]),
     "symnmf_get_factors": (_I, [_P, _P, _P]),
     "symnmf_lai_sketch": (_I, [_P, _I, _I, _P]),
+    "symnmf_lai_sketch_ada": (_I, [_P, _I, _I, _D, _P, _IP, _IP, _DP]),
     "symnmf_get_lai": (_I, [_P, _P, _DP, _IP]),
     "symnmf_set_lai": (_I, [_P, _P, _DP, _I]),
     "symnmf_hals_sweep": (_I, [_P, _I, _I, _I, _DP]),
+    "symnmf_pgncg": (_I, [_P, _I, _I, _I, _DP]),
     "symnmf_leverage": (_I, [_P, _I, _P]),
     "symnmf_lvs_sample": (_I, [_P, _I, _I, _D, _I, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_float), _I,
                                _IP, _IP, _DP]),
@@ -250,6 +252,16 @@ class Solver:
     def lai_sketch(self, l, q, omega=None):
         self._chk(symnmf_lai_sketch(self.h, l, q, _ptr(omega)))
 
+    def lai_sketch_ada(self, l, q_max, tol=1e-3, omega=None):
+        """Adaptive range finder + Apx-EVD; returns dict(checks, passes, nr_hist)."""
+        import numpy as np
+
+        hist = np.zeros(max(q_max, 1))
+        ch, ps = C.c_int(), C.c_int()
+        self._chk(symnmf_lai_sketch_ada(self.h, l, q_max, tol, _ptr(omega), C.byref(ch), C.byref(ps),
+                                        hist.ctypes.data_as(_DP)))
+        return {"checks": ch.value, "passes": ps.value, "nr_hist": hist[: ch.value]}
+
     def set_lai(self, U, lam):
         import numpy as np
 
@@ -284,6 +296,14 @@ class Solver:
         self._chk(symnmf_hals_sweep(self.h, nsweeps, source, rule,
                                     obj.ctypes.data_as(_DP) if record else None))
         return obj[:nsweeps] if record else None
+
+    def pgncg(self, iters, source=SRC_X, s_max=5, record=True):
+        """PGNCG-SymNMF iterations (LAI-PGNCG with source=SRC_LAI); SymNMF objectives if recorded."""
+        import numpy as np
+
+        obj = np.zeros(max(iters, 1)) if record else None
+        self._chk(symnmf_pgncg(self.h, iters, source, s_max, obj.ctypes.data_as(_DP) if record else None))
+        return obj[:iters] if record else None
 
     # -- LvS
     def leverage(self, side):

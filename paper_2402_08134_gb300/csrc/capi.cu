@@ -8,6 +8,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/symnmf.h"
@@ -143,6 +144,14 @@ static symnmf_status check_device_error(symnmf_t h) {
   return SYMNMF_OK;
 }
 
+// Recorded objectives (host, after a synchronising copy): a non-finite one
+// means a NaN or Inf reached the operator or the factors.
+static symnmf_status check_objectives(symnmf_t h, const double* obj, int count) {
+  for (int i = 0; i < count; ++i)
+    if (!isfinite(obj[i])) return fail(h, SYMNMF_ENAN, "non-finite objective");
+  return SYMNMF_OK;
+}
+
 static bool is_dense(int fmt) { return fmt >= SYMNMF_X_DENSE_F64 && fmt <= SYMNMF_X_DENSE_FP8; }
 
 // Workspace for a dense / sparse product of width N.
@@ -224,6 +233,7 @@ symnmf_status product(symnmf_t h, int src, const float* F, int N, int ldf, float
 
 static const double* normx_for(symnmf_t h, int src) {
   if (src == SYMNMF_SRC_LAI) return h->scal + S_LAI_NORM2;
+  if (src == SYMNMF_SRC_COMP) return h->scal + S_COMP_NORM2;
   if (src == SYMNMF_SRC_XHI) return h->scal + S_XHI_NORM2;
   return h->scal + S_NORM2;
 }
@@ -239,27 +249,41 @@ static symnmf_status half_sweep(symnmf_t h, int side, int src, int rule) {
   const float* Y = nullptr;
   const float* U = nullptr;
   const float* M = nullptr;
+  const float* Gf_use = h->Gf[gfix];
+  const double* Gd_use = h->Gd[gfix];
   if (src == SYMNMF_SRC_LAI) {
     // M = Lambda (U^T F) (l x k), Y_r = U_r M fused into the update
     TRY(xcross(h->U, h->l, h->l, Ff, k, k, n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf,
                h->ws, h->counters + 0, h->st));
     U = h->U;
     M = h->Mf;
+  } else if (src == SYMNMF_SRC_COMP) {
+    // Compressed-NMF: M = Q^T F (l x k), G_c = M^T M, Y_r = (X Q)_r M fused into the update
+    TRY(xcross(h->Qk, h->l, h->l, Ff, k, k, n, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, h->Mf, h->ws,
+               h->counters + 0, h->st));
+    TRY(xcross(h->Mf, k, k, h->Mf, k, k, h->l, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gs_d, h->Gs_f, h->ws,
+               h->counters + 0, h->st));
+    U = h->Bk;
+    M = h->Mf;
+    Gf_use = h->Gs_f;
+    Gd_use = h->Gs_d;
   } else {
     TRYS(product(h, src, Ff, k, k, h->Y, k));
     Y = h->Y;
   }
   if (rule == SYMNMF_RULE_HALS)
-    TRY(hals_update(Fu, Ff, n, k, h->Gf[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
+    TRY(hals_update(Fu, Ff, n, k, Gf_use, h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
                     h->counters + 1, h->err, h->st));
   else
-    TRY(bpp_rows(Fu, Ff, n, k, h->Gd[gfix], h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
+    TRY(bpp_rows(Fu, Ff, n, k, Gd_use, h->alpha, Y, k, U, h->l, M, h->scal + S_PART, h->ws,
                  h->counters + 1, h->err, h->st));
   TRY(xcross(Fu, k, k, Fu, k, k, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[gupd], h->Gf[gupd],
              h->ws, h->counters + 2, h->st));
+  // after the H half: the surrogate objective of the operator; for the compressed
+  // problem ||Q^T (W H^T - X)||^2 + alpha ||W - H||^2, whose Gram is G_c
   if (side == 1)
-    TRY(objective(normx_for(h, src), h->Gd[1], h->Gd[0], k, h->scal + S_PART, h->scal + S_ALPHA,
-                  h->obj_ring, h->obj_cnt, OBJ_RING, h->st));
+    TRY(objective(normx_for(h, src), src == SYMNMF_SRC_COMP ? Gd_use : h->Gd[1], h->Gd[0], k, h->scal + S_PART,
+                  h->scal + S_ALPHA, h->obj_ring, h->obj_cnt, OBJ_RING, h->st));
   return SYMNMF_OK;
 }
 
@@ -364,6 +388,10 @@ extern "C" symnmf_status symnmf_create(const symnmf_problem* prob, const symnmf_
   double st3[3];
   if ((e = cudaMemcpy(st3, h->scal + S_MAX, 3 * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return bail(e);
+  if (!isfinite(st3[0]) || !isfinite(st3[1]) || !isfinite(st3[2])) {
+    symnmf_destroy(h);
+    return SYMNMF_ENAN;  // X holds a non-finite entry
+  }
   double mx = st3[0];
   if (p.fmt == SYMNMF_X_CSR_F32 && p.nnz < n * n) mx = fmax(mx, 0.0);  // implicit zeros
   h->alpha = p.alpha > 0 ? p.alpha : mx;
@@ -375,6 +403,10 @@ extern "C" symnmf_status symnmf_create(const symnmf_problem* prob, const symnmf_
   double host_scal[S_COUNT];
   if ((e = cudaMemcpy(host_scal, h->scal, sizeof(host_scal), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return bail(e);
+  if (p.x_hi && (!isfinite(host_scal[S_XHI_MAX]) || !isfinite(host_scal[S_XHI_MAX + 2]))) {
+    symnmf_destroy(h);
+    return SYMNMF_ENAN;  // the float32 copy holds a non-finite entry
+  }
   host_scal[S_ALPHA] = h->alpha;
   host_scal[S_NORM2] = st3[2];
   host_scal[S_MEAN] = st3[1] / ((double)n * (double)n);
@@ -474,6 +506,8 @@ static symnmf_status ensure_lai(symnmf_t h, int l) {
   TRY(dalloc(h, &h->Qa, nl));
   TRY(dalloc(h, &h->Qb, nl));
   TRY(dalloc(h, &h->U, nl));
+  TRY(dalloc(h, &h->Qk, nl));
+  TRY(dalloc(h, &h->Bk, nl));
   TRY(dalloc(h, &h->Mf, (size_t)L * 64));
   TRY(dalloc(h, &h->Sm_d, (size_t)L * L));
   TRY(dalloc(h, &h->V_d, (size_t)L * L));
@@ -517,16 +551,42 @@ static symnmf_status lai_operator_norm(symnmf_t h, int l) {
   return SYMNMF_OK;
 }
 
-extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega) {
-  if (!h) return SYMNMF_EINVAL;
-  if (l < h->k || l > h->o.max_width || q < 0) return fail(h, SYMNMF_EINVAL, "need k <= l <= max_width, q >= 0");
+// Alg. Apx-EVD on the orthonormal basis in Qb (n x l): T = Q^T X Q, T = V Lambda V^T, U = Q V.
+// Q and X Q are kept (Qk, Bk) for the compressed problem, with ||Q^T X||_F^2.
+static symnmf_status apx_evd_from_basis(symnmf_t h, const float* Qb, float* Ts, int l) {
+  (void)Ts;
+  const int64_t n = h->n;
+  TRYS(product(h, SYMNMF_SRC_X, Qb, l, l, h->Bk, l));
+  TRY(cudaMemcpyAsync(h->Qk, Qb, (size_t)n * l * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  TRY(pair_reduce(h->Bk, h->Bk, n * l, h->scal + S_COMP_NORM2, h->ws, h->counters + 6, h->st));
+  TRY(xcross(Qb, l, l, h->Bk, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
+             h->counters + 0, h->st));
+  TRY(jacobi_evd(h->Sm_d, l, h->V_d, h->lam, h->st));
+  TRY(to_float_scaled(h->V_d, l, l, nullptr, h->Sm_f, h->st));
+  TRY(apply_small(Qb, l, l, h->Sm_f, l, n, h->U, l, h->st));
+  TRYS(lai_operator_norm(h, l));
+  h->l = l;
+  h->lai_ready = true;
+  h->lai_from_user = false;
+  h->lai_version++;
+  return SYMNMF_OK;
+}
+
+static symnmf_status sketch_setup(symnmf_t h, int l, const float* omega) {
+  if (l < h->k || l > h->o.max_width) return fail(h, SYMNMF_EINVAL, "need k <= l <= max_width");
   if (h->p.fmt == SYMNMF_X_CSR_F32 && l > 128) return SYMNMF_EINVAL;
   TRYS(ensure_lai(h, l));
-  const int64_t n = h->n;
   if (omega)
-    TRY(cudaMemcpyAsync(h->Om, omega, (size_t)n * l * 4, cudaMemcpyDeviceToDevice, h->st));
+    TRY(cudaMemcpyAsync(h->Om, omega, (size_t)h->n * l * 4, cudaMemcpyDeviceToDevice, h->st));
   else
-    TRY(philox_gaussian(h->Om, n, l, h->p.seed, h->st));
+    TRY(philox_gaussian(h->Om, h->n, l, h->p.seed, h->st));
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float* omega) {
+  if (!h) return SYMNMF_EINVAL;
+  if (q < 0) return fail(h, SYMNMF_EINVAL, "need q >= 0");
+  TRYS(sketch_setup(h, l, omega));
   float* A = h->Qa;
   float* B = h->Qb;
   TRYS(product(h, SYMNMF_SRC_X, h->Om, l, l, A, l));  // Y = X Omega
@@ -537,18 +597,49 @@ extern "C" symnmf_status symnmf_lai_sketch(symnmf_t h, int l, int q, const float
     TRYS(product(h, SYMNMF_SRC_X, B, l, l, A, l));  // X Q
     TRYS(orth(h, A, B, l, j == q - 1));
   }
-  // Apx-EVD: T = Q^T X Q, T = V Lambda V^T, U = Q V
-  TRYS(product(h, SYMNMF_SRC_X, A, l, l, B, l));
-  TRY(xcross(A, l, l, B, l, l, n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Sm_d, nullptr, h->ws,
-             h->counters + 0, h->st));
-  TRY(jacobi_evd(h->Sm_d, l, h->V_d, h->lam, h->st));
-  TRY(to_float_scaled(h->V_d, l, l, nullptr, h->Sm_f, h->st));
-  TRY(apply_small(A, l, l, h->Sm_f, l, n, h->U, l, h->st));
-  TRYS(lai_operator_norm(h, l));
-  h->l = l;
-  h->lai_ready = true;
-  h->lai_version++;
-  return SYMNMF_OK;
+  return apx_evd_from_basis(h, A, B, l);
+}
+
+extern "C" symnmf_status symnmf_lai_sketch_ada(symnmf_t h, int l, int q_max, double tol, const float* omega,
+                                               int* checks_out, int* passes_out, double* nr_hist) {
+  if (!h) return SYMNMF_EINVAL;
+  if (q_max < 0) return fail(h, SYMNMF_EINVAL, "need q_max >= 0");
+  TRYS(sketch_setup(h, l, omega));
+  const int64_t n = h->n;
+  float* Q = h->Qa;  // the current basis
+  float* S = h->Qb;  // the other buffer
+  // every basis whose residual is checked takes all three CholeskyQR passes
+  // (orthonormal to FP32 rounding, which the ||X||^2 - ||B||^2 identity needs);
+  // Q = orth(B^T) only carries the span to the next product unless it is final
+  TRYS(product(h, SYMNMF_SRC_X, h->Om, l, l, Q, l));  // Y = X Omega
+  TRYS(orth(h, Q, S, l, true));
+  int passes = 1, checks = 0;
+  double prev = 0.0;
+  for (int j = 0; j < q_max; ++j) {
+    TRYS(product(h, SYMNMF_SRC_X, Q, l, l, S, l));  // B^T = X^T Q (= X Q)
+    ++passes;
+    // ||Q B - X||_F^2 = ||X||_F^2 - ||B||_F^2: sum of squares of B^T in FP64
+    TRY(pair_reduce(S, S, n * l, h->scal + S_ADA, h->ws, h->counters + 6, h->st));
+    double bb[2], nx2 = 0.0;
+    TRY(cudaMemcpyAsync(bb, h->scal + S_ADA, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    TRY(cudaMemcpyAsync(&nx2, h->scal + S_NORM2, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    TRYS(check_device_error(h));
+    const double nr = sqrt(fmax(nx2 - bb[0], 0.0) / nx2);
+    if (nr_hist) nr_hist[checks] = nr;
+    ++checks;
+    const bool stop = checks >= 2 && prev - nr < tol;
+    prev = nr;
+    TRYS(orth(h, S, Q, l, stop));  // Q = qr(B^T), now in S
+    std::swap(Q, S);
+    if (stop) break;
+    TRYS(product(h, SYMNMF_SRC_X, Q, l, l, S, l));  // Y = X Q
+    ++passes;
+    TRYS(orth(h, S, Q, l, true));  // Q = qr(Y), now in S
+    std::swap(Q, S);
+  }
+  if (checks_out) *checks_out = checks;
+  if (passes_out) *passes_out = passes + 1;  // with the product for T
+  return apx_evd_from_basis(h, Q, S, l);
 }
 
 extern "C" symnmf_status symnmf_set_lai(symnmf_t h, const float* U, const double* lam_host, int l) {
@@ -561,6 +652,7 @@ extern "C" symnmf_status symnmf_set_lai(symnmf_t h, const float* U, const double
   TRY(cudaStreamSynchronize(h->st));  // lam_host may be released on return
   h->l = l;
   h->lai_ready = true;
+  h->lai_from_user = true;
   h->lai_version++;
   return SYMNMF_OK;
 }
@@ -589,9 +681,12 @@ extern "C" symnmf_status symnmf_sketch_features(symnmf_t h, float* out) {
 // ---------------------------------------------------------------- sweeps
 
 static symnmf_status validate_sweep(symnmf_t h, int src, int rule) {
-  if (src == SYMNMF_SRC_LAI && !h->lai_ready) return fail(h, SYMNMF_ESTATE, "LAI sweep before lai_sketch");
+  if (src < 0 || src > 3) return fail(h, SYMNMF_EINVAL, "bad source");
+  if ((src == SYMNMF_SRC_LAI || src == SYMNMF_SRC_COMP) && !h->lai_ready)
+    return fail(h, SYMNMF_ESTATE, "LAI / compressed sweep before lai_sketch");
+  if (src == SYMNMF_SRC_COMP && h->lai_from_user)
+    return fail(h, SYMNMF_ESTATE, "the compressed problem needs a sketch, not set_lai");
   if (src == SYMNMF_SRC_XHI && !h->p.x_hi) return fail(h, SYMNMF_ESTATE, "no float32 copy of X given");
-  if (src < 0 || src > 2) return fail(h, SYMNMF_EINVAL, "bad source");
   if (rule == SYMNMF_RULE_BPP && h->k > 16) return fail(h, SYMNMF_EUNSUPPORTED, "BPP rule needs k <= 16");
   if (rule != SYMNMF_RULE_HALS && rule != SYMNMF_RULE_BPP) return fail(h, SYMNMF_EINVAL, "bad rule");
   return SYMNMF_OK;
@@ -686,6 +781,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
                           h->st));
       TRYS(check_device_error(h));
+      TRYS(check_objectives(h, obj_host + done, chunk));
     }
     done += chunk;
   }
@@ -730,6 +826,7 @@ extern "C" symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, 
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double),
                           cudaMemcpyDeviceToHost, h->st));
       TRYS(check_device_error(h));
+      TRYS(check_objectives(h, obj_host + done, chunk));
     }
     done += chunk;
   }
@@ -835,8 +932,8 @@ static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule) {
 }
 
 static symnmf_status check_lvs(symnmf_t h, int rule) {
-  if (h->p.fmt != SYMNMF_X_CSR_F32 && h->p.fmt != SYMNMF_X_DENSE_F32 && h->p.fmt != SYMNMF_X_DENSE_F64)
-    return fail(h, SYMNMF_EUNSUPPORTED, "LvS needs CSR or dense F32/F64 X");
+  if (h->p.fmt == SYMNMF_X_DENSE_FP8)
+    return fail(h, SYMNMF_EUNSUPPORTED, "LvS needs CSR or dense F32/F64/BF16 X");
   if (rule == SYMNMF_RULE_BPP && h->k > 16) return fail(h, SYMNMF_EUNSUPPORTED, "BPP rule needs k <= 16");
   if (h->p.fmt != SYMNMF_X_CSR_F32 && h->k > 64) return SYMNMF_EUNSUPPORTED;
   return SYMNMF_OK;
@@ -865,11 +962,86 @@ extern "C" symnmf_status symnmf_lvs_iterate(symnmf_t h, int iter0, int iters, do
   return SYMNMF_OK;
 }
 
+// ----------------------------------------------------------------- PGNCG
+
+static symnmf_status ensure_pgncg(symnmf_t h) {
+  if (h->cgR) return SYMNMF_OK;
+  const size_t nk = (size_t)h->n * h->k;
+  TRY(dalloc(h, &h->cgR, nk));
+  TRY(dalloc(h, &h->cgP, nk));
+  TRY(dalloc(h, &h->cgZ, nk));
+  TRY(dalloc(h, &h->cgY, nk));
+  TRY(dalloc(h, &h->cgPtH, (size_t)h->k * h->k));
+  TRY(dalloc(h, &h->cgPtH_d, (size_t)h->k * h->k));
+  TRY(dalloc(h, &h->cg_ws, gn_ws_doubles()));
+  return SYMNMF_OK;
+}
+
+// Y (n x k) = X F for `source` (the LAI operator as U (Lambda (U^T F))).
+static symnmf_status apply_source(symnmf_t h, int source, const float* F, float* Yo) {
+  const int k = h->k;
+  if (source == SYMNMF_SRC_LAI) {
+    TRY(xcross(h->U, h->l, h->l, F, k, k, h->n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf, h->ws,
+               h->counters + 0, h->st));
+    TRY(apply_small(h->U, h->l, h->l, h->Mf, k, h->n, Yo, k, h->st));
+    return SYMNMF_OK;
+  }
+  return product(h, source, F, k, k, Yo, k);
+}
+
+// Y = X H and G = H^T H (FP64 Gd[0], FP32 Gf[0]); with `record`, the SymNMF
+// objective of H appended to the objective ring.
+static symnmf_status gn_products(symnmf_t h, int source, bool record) {
+  const int k = h->k;
+  TRYS(apply_source(h, source, h->H, h->Y));
+  TRY(xcross(h->H, k, k, h->H, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[0], h->Gf[0], h->ws,
+             h->counters + 2, h->st));
+  if (record) {
+    TRY(pair_reduce(h->H, h->Y, h->n * k, h->scal + S_PART2, h->ws, h->counters + 6, h->st));
+    TRY(gn_objective(normx_for(h, source), h->Gd[0], k, h->scal + S_PART2, h->obj_ring, h->obj_cnt, OBJ_RING,
+                     h->st));
+  }
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_pgncg(symnmf_t h, int iters, int source, int s_max, double* obj_host) {
+  if (!h || iters < 0 || s_max < 1 || s_max > 1000 || source == SYMNMF_SRC_COMP) return SYMNMF_EINVAL;
+  TRYS(validate_sweep(h, source, SYMNMF_RULE_HALS));
+  if (iters > OBJ_RING) return fail(h, SYMNMF_EINVAL, "at most 4096 iterations per call");
+  TRYS(ensure_pgncg(h));
+  const int k = h->k;
+  const int64_t nk = h->n * k;
+  double* cg = h->scal + S_CG;
+  TRY(cudaMemsetAsync(h->obj_cnt, 0, sizeof(int), h->st));
+  for (int t = 0; t < iters; ++t) {
+    // the objective of the previous iterate comes with this iteration's product
+    TRYS(gn_products(h, source, obj_host != nullptr && t > 0));
+    TRY(gn_grad(h->H, h->Y, h->Gf[0], h->n, k, h->cgR, h->cgP, h->cgZ, h->cg_ws, h->counters + 7, cg, h->st));
+    for (int s = 0; s < s_max; ++s) {
+      TRY(xcross(h->cgP, k, k, h->H, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->cgPtH_d, h->cgPtH,
+                 h->ws, h->counters + 2, h->st));
+      TRY(gn_hvp(h->H, h->cgP, h->Gf[0], h->cgPtH, h->n, k, h->cgY, h->cg_ws, h->counters + 7, cg, h->st));
+      TRY(gn_update(h->cgP, h->cgY, nk, h->cgR, h->cgZ, h->cg_ws, h->counters + 7, cg, h->st));
+      if (s + 1 < s_max) TRY(gn_dir(h->cgR, nk, h->cgP, cg, h->st));
+    }
+    TRY(gn_project(h->cgZ, nk, h->H, h->W, h->err, h->st));
+  }
+  if (obj_host && iters > 0) {
+    TRYS(gn_products(h, source, true));  // the last iterate's objective
+    TRY(cudaMemcpyAsync(obj_host, h->obj_ring, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    TRYS(check_device_error(h));
+    TRYS(check_objectives(h, obj_host, iters));
+  }
+  TRYS(refresh_grams(h));
+  return SYMNMF_OK;
+}
+
 // -------------------------------------------------------------- residual
 
 extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double* surrogate,
                                          double* proj_grad) {
   if (!h) return SYMNMF_EINVAL;
+  if (source == SYMNMF_SRC_COMP) return fail(h, SYMNMF_EINVAL, "residual of X, the LAI or the float32 copy");
   TRYS(validate_sweep(h, source, SYMNMF_RULE_HALS));
   const int k = h->k;
   const int64_t n = h->n;

@@ -13,8 +13,10 @@
 //                 HBM and needs the deeper buffering);
 //   warp 1      : TMEM allocator + MMA issuer (one thread);
 //   warps 2..5  : epilogue, tcgen05.ld of the accumulator -> FP32 partials.
-// Two TMEM accumulators alternate so that the epilogue of one tile overlaps
-// the MMAs of the next.
+// Two TMEM accumulators alternate so that the epilogue of one accumulation
+// overlaps the MMAs of the next.  An accumulation covers at most 4 k blocks;
+// the epilogue adds the accumulations of a row tile in FP32 registers (round
+// to nearest), so the result carries no accumulator drift over long K.
 //
 // Work split (stream-K): the (row tile, k block) iteration space is cut into
 // gridDim.x equal contiguous ranges, one per CTA, so every SM streams the
@@ -50,6 +52,12 @@ struct TcCfg {
   static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
   static constexpr int NBUF = M2 ? 1 : 2;  // accumulator buffers in TMEM
+  // k blocks accumulated in TMEM before the epilogue adds them into FP32
+  // registers (round to nearest): the tensor core's accumulation drifts low by
+  // a fraction of an FP32 ulp per MMA, which over a whole 20000-long K range
+  // biased X F by ~7e-5 relative.  256-row tiles keep one accumulation per
+  // segment (their single TMEM buffer has no room to alternate).
+  static constexpr int64_t CHUNK = M2 ? (int64_t)1 << 40 : 4;
   static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
   static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
 };
@@ -162,14 +170,15 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
       // ---------------- MMA issuer
       int sa = 0, sb = 0;
       uint32_t pa = 0, pb = 0;
-      int seg = 0;
+      int dr = 0;  // accumulations handed to the epilogue
       bool ok = true;
       int64_t it = it0;
       while (ok && it < it1) {
         const int64_t tile = it / kblocks;
         const int64_t seg_end = min(it1, (tile + 1) * kblocks);
-        const int a = seg % NBUF;
-        const uint32_t use = (uint32_t)(seg / NBUF);
+        const int64_t chunk_end = min(seg_end, it + C::CHUNK);
+        const int a = dr % NBUF;
+        const uint32_t use = (uint32_t)(dr / NBUF);
         if (!mbar_wait(&tempty[a], (use & 1u) ^ 1u, abort_flag)) {
           ok = false;
           break;
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(a * BN);
         const int64_t seg_begin = it;
-        for (; it < seg_end; ++it) {
+        for (; it < chunk_end; ++it) {
           if (!mbar_wait(&fullA[sa], pa, abort_flag) || !mbar_wait(&fullB[sb], pb, abort_flag)) {
             ok = false;
             break;
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
         }
         if (!ok) break;
         umma_commit(&tfull[a]);
-        ++seg;
+        ++dr;
       }
       if (!ok) {
         *abort_flag = 1;
@@ -220,7 +229,49 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
     const int ew = warp & 3;
     int seg = 0;
     int64_t it = it0;
-    while (it < it1) {
+    if constexpr (!M2) {
+      // one thread per row of the 128-row tile: the chunks' accumulators are
+      // added in registers (round to nearest) and the segment's sum written once
+      int dr = 0;
+      while (it < it1) {
+        const int64_t tile = it / kblocks;
+        const int64_t seg_end = min(it1, (tile + 1) * kblocks);
+        float acc[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c) acc[c] = 0.f;
+        bool ok = true;
+        while (it < seg_end) {
+          const int a = dr % NBUF;
+          const uint32_t use = (uint32_t)(dr / NBUF);
+          if (!mbar_wait(&tfull[a], use & 1u, abort_flag)) {
+            *abort_flag = 1;
+            set_error(err, ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll
+          for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[c + q] += v[q];
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[a]);
+          ++dr;
+          it = min(seg_end, it + C::CHUNK);
+        }
+        if (!ok) break;
+        float* dst = partials + (((size_t)blockIdx.x * max_segs + seg) * BM + ew * 32 + lane) * BN;
+#pragma unroll
+        for (int c = 0; c < BN; c += 4) *(float4*)(dst + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+        ++seg;
+      }
+    }
+    while (M2 && it < it1) {
       const int64_t tile = it / kblocks;
       const int64_t seg_end = min(it1, (tile + 1) * kblocks);
       const int a = seg % NBUF;

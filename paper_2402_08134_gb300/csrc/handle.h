@@ -27,7 +27,10 @@ enum {
   S_ZERO = 15,      // stays 0
   S_XHI_MAX = 16,   // 3 slots for the float32 copy
   S_XHI_NORM2 = 18,
-  S_COUNT = 24
+  S_ADA = 20,       // 2 slots: ||B||_F^2 of the adaptive range finder's check
+  S_COMP_NORM2 = 22,  // 2 slots: ||Q^T X||_F^2 of the compressed problem
+  S_CG = 24,        // GN_COUNT slots: scalars of the PGNCG conjugate-gradient loop
+  S_COUNT = 32
 };
 constexpr int OBJ_RING = 4096;
 
@@ -67,14 +70,21 @@ struct symnmf_ctx {
   // LAI
   int l = 0, lai_cap = 0, lai_version = 0;
   bool lai_ready = false;
+  bool lai_from_user = false;  // U, Lambda given by symnmf_set_lai (no basis Q kept)
   float *Om = nullptr, *Qa = nullptr, *Qb = nullptr, *U = nullptr, *Mf = nullptr;
   double *Sm_d = nullptr, *V_d = nullptr, *lam = nullptr, *ev = nullptr;
   float *Sm_f = nullptr, *Rl_f = nullptr;
+  float *Qk = nullptr, *Bk = nullptr;  // the sketch's final basis Q and X Q (n x l each)
   char* eng_ws = nullptr;    // LAI engine workspace
   double* eng_G = nullptr;   // Grams after the engine's last sweep
   unsigned* eng_bar = nullptr;
   double *cq_part = nullptr, *cq_fin = nullptr;  // CholeskyQR engine buffers
   float *cq_Rf = nullptr, *cq_rinv = nullptr;
+
+  // PGNCG: residual R, direction P, step Z, J^T J P (n x k each), P^T H (k x k)
+  float *cgR = nullptr, *cgP = nullptr, *cgZ = nullptr, *cgY = nullptr, *cgPtH = nullptr;
+  double* cgPtH_d = nullptr;
+  double* cg_ws = nullptr;
 
   // LvS
   symnmf::SampleBufs sb{};

@@ -43,7 +43,8 @@ cudaError_t csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val,
 cudaError_t csr_sampled_xf(const int64_t* row_ptr, const int32_t* col, const float* val,
                            const int32_t* idx, const float* wt, const int* s_tot, const float* F,
                            int k, float* Y, cudaStream_t st);
-// Dense version: Y[r, :] += sum_j X[r, i_j] wt_j F[i_j, :] (X symmetric: reads rows i_j).
+// Dense version (fmt F64 / F32 / BF16): Y[r, :] += sum_j X[r, i_j] wt_j F[i_j, :]
+// (X symmetric: reads rows i_j, coalesced).
 cudaError_t dense_sampled_xf(int fmt, const void* X, int64_t ldx, int64_t n, const int32_t* idx,
                              const float* wt, const int* s_tot, int s_cap, const float* F, int k,
                              float* Y, cudaStream_t st);
@@ -169,6 +170,27 @@ size_t cholqr_part_doubles(int l);
 cudaError_t cholqr3(float* S, float* T, int64_t n, int l, double* part, double* fin, double* G, float* Rf,
                     float* rinv, double* ws, unsigned* counter, unsigned* bar, unsigned* err, bool allow_engine,
                     cudaStream_t st, int npass = 3);
+
+// ------------------------------------------------------------------ PGNCG
+// Device scalars of the conjugate-gradient loop (double cg[GN_COUNT]).
+enum { GN_E = 0, GN_E0 = 1, GN_ALPHA = 2, GN_BETA = 3, GN_STOP = 4, GN_COUNT = 8 };
+size_t gn_ws_doubles();
+// R = 2 (H G - Y), P = R, Z = 0, cg[GN_E] = cg[GN_E0] = ||R||^2 (G = H^T H FP32, k <= 64).
+cudaError_t gn_grad(const float* H, const float* Y, const float* G, int64_t n, int k, float* R, float* P, float* Z,
+                    double* ws, unsigned* counter, double* cg, cudaStream_t st);
+// Yc = 2 (P G + H PtH), cg[GN_ALPHA] = cg[GN_E] / <P, Yc> (0 once stopped).
+cudaError_t gn_hvp(const float* H, const float* P, const float* G, const float* PtH, int64_t n, int k, float* Yc,
+                   double* ws, unsigned* counter, double* cg, cudaStream_t st);
+// Z += alpha P, R -= alpha Yc, cg[GN_BETA] = ||R||^2 / cg[GN_E], cg[GN_E] = ||R||^2.
+cudaError_t gn_update(const float* P, const float* Yc, int64_t count, float* R, float* Z, double* ws,
+                      unsigned* counter, double* cg, cudaStream_t st);
+// P = R + beta P.
+cudaError_t gn_dir(const float* R, int64_t count, float* P, const double* cg, cudaStream_t st);
+// H = W = max(H - Z, 0).
+cudaError_t gn_project(const float* Z, int64_t count, float* H, float* W, unsigned* err, cudaStream_t st);
+// out[*cnt] = normX2 - 2 part[0] + sum Gd^2 (the SymNMF objective by the trace trick), *cnt += 1.
+cudaError_t gn_objective(const double* normX2, const double* Gd, int k, const double* part, double* out, int* cnt,
+                         int cap, cudaStream_t st);
 
 // -------------------------------------------------------------------- BPP
 cudaError_t bpp_rows(float* F_upd, const float* F_fix, int64_t n, int k, const double* G,

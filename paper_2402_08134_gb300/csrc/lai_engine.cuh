@@ -13,8 +13,9 @@
 //     1. each CTA updates its rows (Y = U M for its rows, then per row the
 //        columns in order, each using the ones already updated) and writes
 //        one FP32 record of its partial sums over its rows: U^T F_upd,
-//        F_upd^T F_upd (upper 4x4 tiles), and (as hi/lo float pairs of FP64
-//        sums) F_upd . Y and ||F_upd - F_fix||^2;
+//        F_upd^T F_upd (upper 4x4 tiles; FMA sums over four rows folded into
+//        Kahan-compensated totals, each rounded once), and (as hi/lo float
+//        pairs of FP64 sums) F_upd . Y and ||F_upd - F_fix||^2;
 //     2. grid barrier;
 //     3. CTA c sums slice c of the entries over all records in double-float
 //        (Dekker's two-sum; fixed order: deterministic) and writes the FP64
@@ -119,6 +120,14 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2)
   lo = t - (hi - s);
 }
 
+// Kahan-compensated FP32 accumulation: the total is s - c.
+__device__ __forceinline__ void le_kahan(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 // Tiles spread over the block's threads; with fewer tiles than threads, up
 // to LE_MAXRG row groups of threads split the rows, each group writing its
 // own record.
@@ -158,11 +167,19 @@ __device__ __forceinline__ void le_tile_rows(const LeTiles& tl, int tile, int& a
   }
 }
 
-__device__ __forceinline__ void le_clear(float (&acc)[3][16]) {
+__device__ __forceinline__ void le_clear(float (&acc)[3][16], float (&cmp)[3][16]) {
 #pragma unroll
   for (int t = 0; t < 3; ++t)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[t][e] = 0.f;
+    for (int e = 0; e < 16; ++e) acc[t][e] = cmp[t][e] = 0.f;
+}
+
+// Compensated totals -> plain totals (s - c, rounded once) before the record is written.
+__device__ __forceinline__ void le_settle(float (&acc)[3][16], const float (&cmp)[3][16]) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[t][e] -= cmp[t][e];
 }
 
 // Write this CTA's records (one per row group; coalesced float4 stores of the
@@ -312,6 +329,13 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
           if (i < l && j < k) {
             fin[i * k + j] = v;
             st[i * k4 + j] = (float)(a.lam[i] * v);
+            // the H half's rows used M~ = fl32(lambda U^T W), rounded once and shared by
+            // every row, so tr(H^T U M~) misses the exact tr by sum (U^T H) .* (M~ - M):
+            // added back here, where U^T H (this sum, v) and U^T W (fin[0]) are in FP64
+            if (side == 1 && t >= 0) {
+              const double m = a.lam[i] * __ldcg(a.fin + i * k + j);
+              share += 2.0 * v * ((double)(float)m - m);
+            }
           }
         } else {
           int bi, bj;
@@ -401,7 +425,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
   const int R = (int)((a.n * (blockIdx.x + 1)) / gridDim.x - r0);
   const LeTiles tl = le_tiles(l4, k4);
-  float acc[3][16];
+  float acc[3][16], cmp[3][16];
 
   // prologue: the CTA's rows, transposed into shared memory (pads stay zero)
   for (int e = tid; e < (l4 + 3 * k4) * P; e += LE_THREADS) Ut[e] = 0.f;
@@ -452,12 +476,11 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
           for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              float s = acc[t][p * 4 + q];
-              s = fmaf(av[p].x, bv[q].x, s);
+              float s = av[p].x * bv[q].x;
               s = fmaf(av[p].y, bv[q].y, s);
               s = fmaf(av[p].z, bv[q].z, s);
               s = fmaf(av[p].w, bv[q].w, s);
-              acc[t][p * 4 + q] = s;
+              le_kahan(acc[t][p * 4 + q], cmp[t][p * 4 + q], s);
             }
         }
       }
@@ -465,8 +488,9 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
   };
 
   // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
-  le_clear(acc);
+  le_clear(acc, cmp);
   accumulate(Ht);
+  le_settle(acc, cmp);
   le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
   unsigned epoch = 0;
   if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
@@ -518,8 +542,9 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
       }
       if (bad) set_error(a.err, ERR_NAN);
       __syncthreads();
-      le_clear(acc);
+      le_clear(acc, cmp);
       accumulate(Fu);
+      le_settle(acc, cmp);
       le_finish(a, tl, acc, red, trv, ddv);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
       le_reduce_slice(a, side, t, red, shd);
@@ -568,7 +593,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
   const int64_t r1 = (a.n * (blockIdx.x + 1)) / gridDim.x;
   const LeTiles tl = le_tiles(l4, k4);
-  float acc[3][16];
+  float acc[3][16], cmp[3][16];
 
   // pad columns (c >= l of U, c >= k of the factors) are zero once and for all;
   // rows past a tile's end are never read
@@ -604,24 +629,36 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
         le_tile_rows(tl, tile, ab, bb, au);
         const float* A = au ? Us : Fu;
         const int sa = au ? us : fs, ai = 4 * ab, bj = 4 * bb;
-        for (int rr = tl.my_rg; rr < rows; rr += tl.RG) {
-          float av[4], bv[4];
+        // FMA sums over up to four of the group's rows, folded into the Kahan totals
+        for (int r4 = tl.my_rg; r4 < rows; r4 += 4 * tl.RG) {
+          float part[16];
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            av[p] = A[rr * sa + ai + p];
-            bv[p] = Fu[rr * fs + bj + p];
+          for (int e = 0; e < 16; ++e) part[e] = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int rr = r4 + u * tl.RG;
+            if (rr < rows) {
+              float av[4], bv[4];
+#pragma unroll
+              for (int p = 0; p < 4; ++p) {
+                av[p] = A[rr * sa + ai + p];
+                bv[p] = Fu[rr * fs + bj + p];
+              }
+#pragma unroll
+              for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) part[p * 4 + q] = fmaf(av[p], bv[q], part[p * 4 + q]);
+            }
           }
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[t][p * 4 + q] = fmaf(av[p], bv[q], acc[t][p * 4 + q]);
+          for (int e = 0; e < 16; ++e) le_kahan(acc[t][e], cmp[t][e], part[e]);
         }
       }
     }
   };
 
   // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
-  le_clear(acc);
+  le_clear(acc, cmp);
   for (int64_t b = r0; b < r1; b += TR) {
     const int rows = (int)min((int64_t)TR, r1 - b);
     stage(b, rows, nullptr, a.H);
@@ -629,6 +666,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
     accumulate(rows);
     __syncthreads();
   }
+  le_settle(acc, cmp);
   le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
   unsigned epoch = 0;
   if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
@@ -644,7 +682,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
       const float* Ffix = side ? a.W : a.H;
       float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
       bool bad = false;
-      le_clear(acc);
+      le_clear(acc, cmp);
       for (int64_t b = r0; b < r1; b += TR) {
         const int rows = (int)min((int64_t)TR, r1 - b);
         stage(b, rows, Ffix, Fupd);
@@ -684,6 +722,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
         __syncthreads();
       }
       if (bad) set_error(a.err, ERR_NAN);
+      le_settle(acc, cmp);
       le_finish(a, tl, acc, red, trv, ddv);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
       le_reduce_slice(a, side, t, red, shd);

@@ -9,6 +9,8 @@
 //   dense_sampled_xf: the same product for a dense X.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -198,6 +200,9 @@ cudaError_t dense_sampled_xf(int fmt, const void* X, int64_t ldx, int64_t n, con
     dense_sampled_kernel<float><<<grid, 128, 0, st>>>((const float*)X, ldx, n, idx, wt, s_tot, F, k, Y);
   else if (fmt == 0)
     dense_sampled_kernel<double><<<grid, 128, 0, st>>>((const double*)X, ldx, n, idx, wt, s_tot, F, k, Y);
+  else if (fmt == 2)
+    dense_sampled_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>((const __nv_bfloat16*)X, ldx, n, idx, wt, s_tot,
+                                                               F, k, Y);
   else
     return cudaErrorInvalidValue;
   count_launches(1);

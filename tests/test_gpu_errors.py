@@ -37,16 +37,37 @@ def test_leverage_of_a_factor_with_a_zero_column_is_not_spd(S):
     assert lev.sum() == pytest.approx(6.0, rel=1e-5)
 
 
-def test_nan_in_x_reaches_a_factor_and_is_reported(S):
+def test_nonfinite_x_is_reported_at_create(S):
     rng = np.random.default_rng(3)
     A = rng.random((256, 256))
     X = 0.5 * (A + A.T)
-    X[17, 40] = X[40, 17] = np.nan
-    s = S.Solver(t32(X), 5, alpha=1.0, seed=4)
-    s.set_factors(t32(uniform_factor(256, 5, seed=5)))
-    with pytest.raises(S.SymNMFError) as e:
-        s.sweep(2)  # recording the objectives synchronises and reads the error word
-    assert e.value.status == S.ENAN
+    for bad in (np.nan, np.inf):
+        Xb = X.copy()
+        Xb[17, 40] = Xb[40, 17] = bad
+        with pytest.raises(S.SymNMFError) as e:
+            S.Solver(t32(Xb), 5, alpha=1.0, seed=4)
+        assert e.value.status == S.ENAN
+        # the same through the float32 copy of a BF16 problem
+        with pytest.raises(S.SymNMFError) as e:
+            S.Solver(t32(X).to(torch.bfloat16), 5, alpha=1.0, x_hi=t32(Xb))
+        assert e.value.status == S.ENAN
+
+
+def test_nan_in_the_operator_reaches_the_objective_and_is_reported(S):
+    # a NaN eigenvalue given through set_lai: the recorded LAI objective is non-finite
+    rng = np.random.default_rng(4)
+    A = rng.random((256, 256))
+    X = 0.5 * (A + A.T)
+    Q, _ = np.linalg.qr(rng.standard_normal((256, 12)))
+    lam = np.linspace(10.0, 1.0, 12)
+    lam[5] = np.nan
+    for mode in (0, 1):  # persistent engine, separate kernels
+        s = S.Solver(t32(X), 5, alpha=1.0, seed=4, max_width=12, lai_mode=mode)
+        s.set_lai(t32(Q), lam)
+        s.set_factors(t32(uniform_factor(256, 5, seed=5)))
+        with pytest.raises(S.SymNMFError) as e:
+            s.sweep(2, source=S.SRC_LAI)
+        assert e.value.status == S.ENAN
 
 
 def test_nonfinite_or_negative_start_is_rejected(S):

@@ -61,6 +61,34 @@ def test_tcgen05_bf16_product(S, n, N):
     assert (np.abs(Y - ref) <= bound).all(), np.abs(Y - ref).max()
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("N", [20, 50, 128])
+def test_tcgen05_product_is_unbiased_over_long_k(S, fmt, N):
+    # nonnegative X and F (as in SymNMF): the mean signed relative error of Y against the exact
+    # product of the rounded operands must vanish.  Tensor-core accumulation drifts low by a
+    # fraction of an FP32 ulp per MMA; over K = 20000 in one accumulator that was 7e-5, which
+    # the trace-trick residual (a difference of terms ~ ||X||^2) turns into a 4e-3 error in NR
+    n = 20000
+    rng = np.random.default_rng(N + (fmt == "fp8"))
+    Xt = torch.rand((n, n), device="cuda", generator=torch.Generator(device="cuda").manual_seed(N))
+    F = rng.random((n, N)).astype(np.float32)
+    Ft = t32(F)
+    if fmt == "bf16":
+        Xq = Xt.to(torch.bfloat16)
+        Y = S.dense_xf(Xq, Ft, gemm=S.GEMM_TC)
+        ref = Xq.double() @ Ft.to(torch.bfloat16).double()
+    else:
+        x8, rs = S.quantize_fp8(Xt)
+        Y = S.dense_xf(x8, Ft, row_scale=rs, gemm=S.GEMM_TC)
+        Xe = x8[:, :n].view(torch.float8_e4m3fn).double() * rs.double()[:, None]
+        cs = Ft.abs().amax(dim=0) / 448.0
+        Fq = (Ft / cs).to(torch.float8_e4m3fn).double() * cs.double()
+        ref = Xe @ Fq
+    rel = ((Y.double() - ref) / ref).cpu().numpy()
+    assert abs(rel.mean()) < 1e-6, rel.mean()
+    assert np.abs(rel).max() < 1e-4
+
+
 @pytest.mark.parametrize("n,N", [(1000, 20), (2064, 50), (4096, 128), (3000, 256), (333, 160)])
 def test_tcgen05_fp8_product(S, n, N):
     rng = np.random.default_rng(n + N)

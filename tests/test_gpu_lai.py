@@ -132,3 +132,57 @@ def test_lai_engine_and_per_kernel_path_match_oracle(S, n, k, l):
         s.set_factors(t32(Hi))
         got = s.sweep(30, source=S.SRC_LAI)
         assert rel_err(got, ref).max() < 1e-4, (mode, rel_err(got, ref).max())
+
+
+@pytest.mark.parametrize("q_max", [0, 1, 8])
+def test_ada_rrf_matches_oracle(S, q_max):
+    # Alg. Ada-RRF on the GPU (FP32 X, same Omega): the same number of checks, residuals within
+    # FP32 rounding of the oracle's, and the same LAI operator
+    X, _ = _gmm_kernel(3000, 10, 6, seed=12)
+    l = 22
+    Om = gaussian_sketch(3000, l, seed=13)
+    s = S.Solver(t32(X), 6, max_width=l)
+    got = s.lai_sketch_ada(l, q_max, 1e-3, t32(Om))
+    Uo, lo, hist, passes = O.apx_evd_ada(X, Om, q_max, 1e-3)
+    assert got["checks"] == len(hist) and got["passes"] == passes
+    np.testing.assert_allclose(got["nr_hist"], hist, rtol=0, atol=2e-5)
+    U, lam = s.lai()
+    Ug = np64(U)
+    F = uniform_factor(3000, 6, seed=14)
+    ref = O.lai_product(Uo, lo, F)
+    assert np.linalg.norm(Ug @ (lam[:, None] * (Ug.T @ F)) - ref) / np.linalg.norm(ref) < 1e-4
+
+
+def test_ada_rrf_stops_early_on_a_low_rank_matrix(S):
+    X, _, _ = planted_dense(n=800, k=8, sigma=0.0, seed=3)
+    s = S.Solver(t64(X), 8, max_width=26)
+    got = s.lai_sketch_ada(26, 10, 1e-3)
+    assert got["checks"] == 2 and got["passes"] == 5
+    # sqrt(||X||^2 - ||B||^2) / ||X|| from FP32 products cancels down to ~sqrt(FP32 eps)
+    assert got["nr_hist"][0] < 1e-3
+    U, lam = s.lai()
+    Ug = np64(U)
+    assert np.linalg.norm(X - (Ug * lam) @ Ug.T) / np.linalg.norm(X) < 1e-5
+
+
+@pytest.mark.parametrize("rule", ["hals", "bpp"])
+def test_compressed_sweeps_match_oracle(S, rule):
+    # Compressed-SymNMF on the GPU's sketch basis (same Omega) against the oracle's on its
+    # Householder basis: the compressed problem depends only on the projector Q Q^T
+    X, _ = _gmm_kernel(3000, 10, 6, seed=15)
+    k, l, q = 6, 22, 2
+    Om = gaussian_sketch(3000, l, seed=16)
+    Hi = (uniform_factor(3000, k, seed=17) * O.init_scale(X, k)).astype(np.float32).astype(np.float64)
+    r = S.RULE_HALS if rule == "hals" else S.RULE_BPP
+    s = S.Solver(t32(X), k, max_width=l)
+    s.lai_sketch(l, q, t32(Om))
+    s.set_factors(t32(Hi))
+    got = s.sweep(30, source=S.SRC_COMP, rule=r)
+    Q = O.rrf(X, Om, q)
+    W, H, ref = O.compressed_symnmf(X, Q, Hi, O.default_alpha(X), 30, rule=rule)
+    assert rel_err(got, ref).max() < 1e-4, rel_err(got, ref).max()
+    Hg, Wg = s.factors()
+    np.testing.assert_allclose(np64(Hg), H, rtol=0, atol=1e-3 * np.abs(H).max())
+    # not a residual source
+    with pytest.raises(S.SymNMFError):
+        s.residual(S.SRC_COMP)

@@ -1,6 +1,7 @@
 """Pins for the oracle's range finder, Apx-EVD, LAI products and leverage scores."""
 
 import numpy as np
+import pytest
 
 from oracle import symnmf as O
 from synth import gaussian_sketch, gmm_points, kernel_matrix_numpy, median_pair_distance, planted_dense, uniform_factor
@@ -92,3 +93,55 @@ def test_leverage_scores_rank_deficient():
     Us, s, _ = np.linalg.svd(F, full_matrices=False)
     r = (s > 1e-10 * s[0]).sum()
     np.testing.assert_allclose(lev, (Us[:, :r] ** 2).sum(1), rtol=1e-9, atol=1e-13)
+
+
+def _projector_distance(Q1, Q2):
+    return float(np.linalg.norm(Q1 @ Q1.T - Q2 @ Q2.T, 2))
+
+
+def test_ada_rrf_without_stopping_is_the_fixed_q_range_finder():
+    # never stopping (tol = -inf) after q_max checks leaves the basis of Alg. RRF with q = q_max
+    rng = np.random.default_rng(21)
+    n, l = 300, 12
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    X = (V * np.exp(-np.arange(n) / 15.0)) @ V.T
+    Om = rng.standard_normal((n, l))
+    for q in (0, 1, 3):
+        Qa, hist, passes = O.ada_rrf(X, Om, q, tol=-np.inf)
+        assert len(hist) == q and passes == 1 + 2 * q
+        assert _projector_distance(Qa, O.rrf(X, Om, q)) < 1e-10
+
+
+def test_ada_rrf_residuals_are_the_qb_residuals_of_the_checked_bases():
+    # each recorded residual is ||X - Q Q^T X|| / ||X|| of the basis checked, computed directly
+    rng = np.random.default_rng(22)
+    n, l = 200, 10
+    A = rng.standard_normal((n, 30))
+    X = A @ A.T + 0.01 * np.eye(n)
+    Om = rng.standard_normal((n, l))
+    _, hist, _ = O.ada_rrf(X, Om, 4, tol=-np.inf)
+    Q, _ = np.linalg.qr(X @ Om)
+    for j in range(4):
+        direct = np.linalg.norm(X - Q @ (Q.T @ X)) / np.linalg.norm(X)
+        assert hist[j] == pytest.approx(direct, rel=1e-8, abs=1e-12)
+        Q, _ = np.linalg.qr(X @ Q)
+        Q, _ = np.linalg.qr(X @ Q)
+
+
+def test_ada_rrf_stops_once_the_residual_stalls():
+    # rank(X) <= l: the first check already captures X (residual ~ 0), the second finds no
+    # further decrease and stops; the EVD then reproduces X exactly
+    X, _, _ = planted_dense(n=300, k=6, sigma=0.0, seed=4)
+    Om = np.random.default_rng(23).standard_normal((300, 12))
+    Q, hist, passes = O.ada_rrf(X, Om, 10, tol=1e-3)
+    assert len(hist) == 2 and hist[0] < 1e-12 and passes == 4
+    U, lam, _, passes_evd = O.apx_evd_ada(X, Om, 10)
+    assert passes_evd == 5
+    assert np.linalg.norm(X - (U * lam) @ U.T) / np.linalg.norm(X) < 1e-12
+    # a slowly decaying spectrum keeps improving by more than tol for a while
+    rng = np.random.default_rng(24)
+    V, _ = np.linalg.qr(rng.standard_normal((300, 300)))
+    Xs = (V * (1.0 / (1.0 + np.arange(300)) ** 0.5)) @ V.T
+    _, hs, _ = O.ada_rrf(Xs, rng.standard_normal((300, 12)), 10, tol=1e-3)
+    assert all(a - b >= 1e-3 for a, b in zip(hs[:-2], hs[1:-1]))
+    assert len(hs) == 10 or hs[-2] - hs[-1] < 1e-3

@@ -70,7 +70,7 @@ def test_gram_noalloc_leaves_default_pool_untouched(S):
     rt = _cudart()
     if rt is None or not os.path.exists("/usr/local/cuda"):
         pytest.skip("CUDA runtime library not found")
-    USED_HIGH, USED_CUR = 7, 6  # cudaMemPoolAttrUsedMemHigh, cudaMemPoolAttrUsedMemCurrent
+    USED_CUR, USED_HIGH = 7, 8  # cudaMemPoolAttrUsedMemCurrent, cudaMemPoolAttrUsedMemHigh
     pool = C.c_void_p()
     assert rt.cudaDeviceGetDefaultMemPool(C.byref(pool), torch.cuda.current_device()) == 0
 
