@@ -32,6 +32,9 @@ Also reported (unless --no-forms):
 - the tensor-core product at widths past the BF16 ridge (N = 256, 512);
 - the batched grouped solver (64 problems x 4 restarts) against the plain FP32
   solves of all 256, one after another;
+- the sparse LvS workload (n = 10^6 SBM, k = 64): per-iteration speedup of
+  LvS-HALS over full HALS, its sampling / products / update split, residuals
+  against the oracle's, and time to the oracle LvS's residual;
 - the learned warm start at reduced size;
 - the end-to-end time through the public API with X copied in from pinned host
   memory (the `e2e` key);
@@ -89,7 +92,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP8, tensor, batched and learned forms")
-    ap.add_argument("--forms", default="fp8,tensor,batched,learned",
+    ap.add_argument("--forms", default="fp8,tensor,batched,lvs,learned",
                     help="comma-separated subset of the forms to run")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch sweep kernels one by one instead of replaying recorded graphs (for profilers)")
@@ -336,24 +339,19 @@ def batched_form(S, dev, sweeps=100):
     import numpy as np
     import torch
 
-    from synth import batched_problem_specs
+    from synth import batched_problem_specs, dense_sbm
 
     specs = batched_problem_specs(64, seed=0)
     Xs, Xf = [], []
     for p, sp in enumerate(specs):
         m, kc = sp["n"], sp["k"]
-        g = torch.Generator(device=dev).manual_seed(1000 + p)
-        lab = torch.randperm(m, generator=g, device=dev) * kc // m
-        P = torch.where(lab[:, None] == lab[None, :], 0.3, 0.015)
-        A = torch.triu(torch.rand((m, m), generator=g, device=dev) < P, 1)
-        A = A | A.T
-        A.fill_diagonal_(True)
+        A = torch.tensor(dense_sbm(m, kc, seed=1000 + p)[0], device=dev)
         ld = (m + 7) // 8 * 8
         buf = torch.zeros((m, ld), dtype=torch.bfloat16, device=dev)
         buf[:, :m] = A.to(torch.bfloat16)
         Xs.append(buf)
-        Xf.append(A.to(torch.float32))
-        del A, P
+        Xf.append(A)
+        del A
     b = S.Batch(Xs, [sp["k"] for sp in specs], restarts=4)
     b.init_random(True)
     b.sweep(2, record=False)  # records the sweep graph
@@ -403,6 +401,89 @@ def batched_form(S, dev, sweeps=100):
         ref = np.asarray(gold["nr"])
         out["nr_max_abs_diff_vs_oracle"] = float(np.max(np.abs(np.asarray(nr_b) - ref)))
         out["nr_within_1e-3_of_oracle"] = bool(np.all(np.abs(np.asarray(nr_b) - ref) <= 1e-3))
+    return out
+
+
+def lvs_form(S, dev):
+    """The sparse LvS workload: stochastic block model, n = 10^6 nodes, 64 communities, mean degree 30,
+    CSR FP32 with self-loops; k = 64, s = ceil(8 k ln k) = 2130 sampled rows, tau = 1/s, Philox key 3.
+
+    Reported: the per-iteration time of LvS-HALS against the full-X HALS sweep (the paper's OAG
+    speedup), LvS's time split into sampling / sampled products / update (the paper's Sampling /
+    MM / Solve buckets), the residuals after 50 iterations against the FP64 oracle's (stored in
+    tests/golden/c3_reference.json), and the time each form needs to reach the residual the
+    oracle's LvS-SymNMF reaches in 50 iterations (+1e-6: on this graph the normalized residual
+    lives in its fifth decimal), with a residual check every 5 iterations."""
+    import torch
+
+    from synth import lvs_sample_count, sbm_csr
+
+    n, k = 1_000_000, 64
+    g = sbm_csr(n=n, c=64, avg_deg=30.0, ratio=20.0, seed=0)
+    csr = tuple(torch.tensor(g[x], device=dev) for x in ("row_ptr", "col", "val"))
+    del g
+    sc = lvs_sample_count(k)
+    tau = 1.0 / sc
+    gold = golden("c3_reference.json")
+    target = gold["lvs_nr"]["50"] + 1e-6 if gold else None
+    sv = S.Solver(csr=csr, k=k, n=n, seed=3, use_graph=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    def to_target(lvs):
+        sv.init_random(True)
+        it, checks, nr = 0, 0, float("inf")
+        while it < 100:
+            if lvs:
+                sv.lvs_iterate(5, tau, sc, iter0=it)
+            else:
+                sv.sweep(5, S.SRC_X, record=False)
+            it += 5
+            nr = sv.residual(S.SRC_X)[0]
+            checks += 1
+            if target is not None and nr <= target:
+                break
+        return {"iterations": it, "checks": checks, "nr": nr, "reached": target is not None and nr <= target}
+
+    out = {"config": "SBM n=1e6, 64 communities, mean degree 30, CSR FP32 + self-loops, k=64, "
+                     f"s={sc}, tau=1/s, residual check every 5 iterations", "target": target}
+    sv.init_random(True)
+    sv.lvs_iterate(2, tau, sc)  # warm-up: buffers, sampler
+    sv.sweep(1, S.SRC_X, record=False)
+    # per-iteration time (both halves) over 20 iterations each, and LvS's buckets
+    sv.init_random(True)
+    t_lvs, _ = timed(lambda: sv.lvs_iterate(20, tau, sc))
+    sv.init_random(True)
+    t_full, _ = timed(lambda: sv.sweep(20, S.SRC_X, record=False))
+    sv.init_random(True)
+    sv.profile(True)
+    sv.lvs_iterate(20, tau, sc)
+    samp, mm, upd, halves = sv.profile_read_lvs()
+    sv.profile(False)
+    out["ms_per_iteration"] = {"lvs_hals": t_lvs / 20 * 1e3, "full_hals": t_full / 20 * 1e3,
+                               "speedup": t_full / t_lvs}
+    out["lvs_buckets_ms_per_iteration"] = {"sampling": samp / 10, "mm": mm / 10, "solve": upd / 10}
+    # residual after 50 iterations against the oracle's
+    sv.init_random(True)
+    sv.lvs_iterate(50, tau, sc)
+    nr_lvs = sv.residual(S.SRC_X)[0]
+    sv.init_random(True)
+    sv.sweep(50, S.SRC_X, record=False)
+    nr_full = sv.residual(S.SRC_X)[0]
+    out["nr_after_50"] = {"lvs_hals": nr_lvs, "full_hals": nr_full,
+                          "oracle_lvs": gold["lvs_nr"]["50"] if gold else None,
+                          "oracle_full": gold["plain_nr"]["50"] if gold else None}
+    for name, lvs in (("lvs_hals", True), ("full_hals", False)):
+        t, r = timed(lambda: to_target(lvs))
+        out[f"to_target_{name}"] = dict(r, s=t)
+    sv.close()
     return out
 
 
@@ -545,6 +626,8 @@ def run_ours(args):
     del x8, rs8
     if "batched" in forms:
         out["batched_c4"] = batched_form(S, dev)
+    if "lvs" in forms:
+        out["lvs_c3"] = lvs_form(S, dev)
     if "learned" in forms:
         out["learned_small"] = learned_form()
 

@@ -209,6 +209,46 @@ symnmf_status symnmf_hals_sweep(symnmf_t h, int nsweeps, int source, int rule, d
  * synchronises only then.  iters <= 4096, 1 <= s_max <= 1000. */
 symnmf_status symnmf_pgncg(symnmf_t h, int iters, int source, int s_max, double* obj_host);
 
+/* The experiments' schedule (section "Experimental Results", WoS setup), run
+ * end to end on the device:
+ *   1. with method SYMNMF_SRC_LAI or SYMNMF_SRC_COMP, the sketch by the
+ *      adaptive range finder (symnmf_lai_sketch_ada with l, q_max, ada_tol);
+ *   2. iterations on `method`'s operator (HALS / BPP sweeps by `rule`, or
+ *      PGNCG iterations when algo = 1) until the normalized residual
+ *      sqrt(objective / ||operator||^2), read after every iteration, has
+ *      fallen by less than stop_tol in each of stop_count consecutive
+ *      iterations (the experiments use 1e-4 and 4), or max_iters;
+ *   3. with refine != 0 and a sketched method, Iterative Refinement: the
+ *      same iterations and stopping rule on X itself (its float32 copy when
+ *      the problem has one), at most max_refine.
+ * The start is the handle's current factors.  The report gives the
+ * sketch's checks and passes, the iterations of each phase, and the true
+ * normalized residual ||X - W H^T|| / ||X|| at the end (||X - H H^T|| / ||X||
+ * for PGNCG) against X (or its float32 copy).  Synchronises every iteration. */
+typedef struct {
+  int32_t method;      /* SYMNMF_SRC_X, SYMNMF_SRC_LAI or SYMNMF_SRC_COMP */
+  int32_t algo;        /* 0: alternating updates by `rule`; 1: PGNCG (X or LAI only) */
+  int32_t rule;        /* SYMNMF_RULE_HALS or SYMNMF_RULE_BPP */
+  int32_t l;           /* sketch width */
+  int32_t q_max;       /* at most this many power iterations (Ada-RRF) */
+  int32_t stop_count;  /* consecutive small decreases that stop a phase (>= 1) */
+  int32_t max_iters;   /* cap of the first phase */
+  int32_t refine;      /* 1: Iterative Refinement after a sketched phase */
+  int32_t max_refine;  /* cap of the refinement phase */
+  int32_t s_max;       /* CG steps per PGNCG iteration */
+  double ada_tol;      /* Ada-RRF: stop when the QB residual falls by less */
+  double stop_tol;     /* per-iteration decrease of the normalized residual */
+} symnmf_schedule;
+
+typedef struct {
+  int32_t checks, passes;    /* the adaptive range finder's residual checks and X passes */
+  int32_t iters, refine_iters;
+  double nr_phase;           /* normalized residual of the operator when phase 2 stopped */
+  double nr_final;           /* true-X normalized residual at the end */
+} symnmf_report;
+
+symnmf_status symnmf_solve(symnmf_t h, const symnmf_schedule* sched, symnmf_report* report);
+
 /* ------------------------------------------------------------ LvS (Alg. 2) */
 
 /* Leverage scores of the fixed factor (side 0: H, used to update W; side 1:
@@ -255,8 +295,13 @@ symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double
 /* -------------------------------------------------- standalone kernels */
 
 /* Y = X F for a dense X (fmt F64/F32/BF16/FP8, ld ldx, FP8 with row_scale),
- * F device float [n x N] (ld ldf), Y device float [n x N] (ld ldy), N <= 256.
- * gemm = SYMNMF_GEMM_*.  Stream-ordered, no synchronisation. */
+ * F device float [n x N] (ld ldf), Y device float [n x N] (ld ldy); N <= 512
+ * for BF16 / FP8 X (tcgen05: 128-row tiles up to 128 columns, 256-row tiles
+ * at 256, two N = 256 MMAs per k step at 512), N <= 128 for F32 / F64 X.
+ * Up to 128 columns the tensor-core accumulation is flushed to FP32 every 8
+ * k blocks; wider products accumulate a whole K segment in TMEM, which the
+ * tensor core rounds low by about 2e-8 relative per MMA (~6e-5 at n = 20000).
+ * gemm = SYMNMF_GEMM_*.  Synchronises the stream (BF16 / FP8). */
 symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, const float* row_scale, int64_t n,
                               const float* F, int ldf, int N, float* Y, int ldy, int gemm, void* stream);
 /* Y = X F for CSR X (row_ptr int64[n+1], col int32[nnz], val float[nnz]); F, Y device
@@ -322,6 +367,17 @@ symnmf_status symnmf_profile_standalone_read(double* total_ms, int64_t* launches
  * updates, U^T F, upper F^T F), plus a prologue of n (l k + k (k + 1) / 2),
  * two FLOPs each.  Resets the record. */
 symnmf_status symnmf_profile_read_engine(symnmf_t h, double* total_ms, int64_t* launches, double* flops);
+
+/* The LvS iterations' time split (the buckets of the paper's per-iteration
+ * breakdown, section "Microsoft Open Academic Graph"): while symnmf_profile is
+ * enabled, every half of symnmf_lvs_iterate is bracketed by CUDA events on the
+ * handle's stream.  Read (synchronises; resets the record): sampling_ms =
+ * leverage scores (Gram, FP64 Cholesky and inverse, row pass) and the hybrid
+ * sampler; products_ms = the sampled products Y = X S^T S F and
+ * G = F^T S^T S F ("MM"); update_ms = the Update() rule ("Solve"); halves =
+ * the halves recorded. */
+symnmf_status symnmf_profile_read_lvs(symnmf_t h, double* sampling_ms, double* products_ms, double* update_ms,
+                                      int64_t* halves);
 
 /* Number of kernels this library has launched in this process (graph replays
  * count each kernel node). */

@@ -476,6 +476,51 @@ def lvs_symnmf(X, H0, alpha, iters, s, tau, seed, W0=None, rule="hals", trace=No
     return W, H
 
 
+# ------------------------------------------------------- the experiments' schedule
+
+
+def stop_rule_phase(step, max_iters, tol=1e-4, count=4):
+    """Iterate `step()` (returning the normalized residual after the iteration) until the residual
+    has fallen by less than `tol` in `count` consecutive iterations (section "Experimental
+    Results": 1e-4 for four consecutive iterations), or max_iters.  Returns (iterations, last NR)."""
+    prev, nr, small, t = 0.0, 0.0, 0, 0
+    while t < max_iters:
+        nr = step()
+        t += 1
+        if t > 1:
+            small = small + 1 if prev - nr < tol else 0
+        prev = nr
+        if small >= count:
+            break
+    return t, nr
+
+
+def lai_schedule(X, Omega, H0, alpha, q_max=10, ada_tol=1e-3, tol=1e-4, count=4, max_iters=500,
+                 refine=True, max_refine=200, rule="hals"):
+    """LAI-HALS / LAI-BPP with the experiments' schedule: Ada-RRF + Apx-EVD, LAI sweeps to the
+    stopping rule (NR of the surrogate against U Lambda U^T), then Iterative Refinement sweeps on X
+    with the same rule.  Returns dict(W, H, passes, iters, refine_iters, nr_final)."""
+    U, lam, hist, passes = apx_evd_ada(X, Omega, q_max, ada_tol)
+    state = {"W": np.array(H0, dtype=np.float64, copy=True), "H": np.array(H0, dtype=np.float64, copy=True)}
+    lai_nx2 = float((lam ** 2).sum())
+    nx2 = float((X * X).sum())
+
+    def lai_step():
+        W, H, objs = lai_symnmf(U, lam, state["H"], alpha, 1, W0=state["W"], rule=rule)
+        state["W"], state["H"] = W, H
+        return math.sqrt(max(objs[-1], 0.0) / lai_nx2)
+
+    def full_step():
+        W, H, objs = hals_symnmf(X, state["H"], alpha, 1, W0=state["W"], rule=rule)
+        state["W"], state["H"] = W, H
+        return math.sqrt(max(objs[-1], 0.0) / nx2)
+
+    iters, _ = stop_rule_phase(lai_step, max_iters, tol, count)
+    riters = stop_rule_phase(full_step, max_refine, tol, count)[0] if refine else 0
+    return dict(W=state["W"], H=state["H"], passes=passes, checks=len(hist), iters=iters, refine_iters=riters,
+                nr_final=normalized_residual(X, state["W"], state["H"]))
+
+
 # ----------------------------------------------------------------- helpers
 
 

@@ -59,6 +59,17 @@ class symnmf_options(C.Structure):
                 ("max_samples", C.c_int32), ("lai_mode", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
+class symnmf_schedule(C.Structure):
+    _fields_ = [("method", C.c_int32), ("algo", C.c_int32), ("rule", C.c_int32), ("l", C.c_int32),
+                ("q_max", C.c_int32), ("stop_count", C.c_int32), ("max_iters", C.c_int32), ("refine", C.c_int32),
+                ("max_refine", C.c_int32), ("s_max", C.c_int32), ("ada_tol", C.c_double), ("stop_tol", C.c_double)]
+
+
+class symnmf_report(C.Structure):
+    _fields_ = [("checks", C.c_int32), ("passes", C.c_int32), ("iters", C.c_int32), ("refine_iters", C.c_int32),
+                ("nr_phase", C.c_double), ("nr_final", C.c_double)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _I64 = C.c_int64
@@ -80,6 +91,7 @@ _SIGS = {
     "symnmf_set_lai": (_I, [_P, _P, _DP, _I]),
     "symnmf_hals_sweep": (_I, [_P, _I, _I, _I, _DP]),
     "symnmf_pgncg": (_I, [_P, _I, _I, _I, _DP]),
+    "symnmf_solve": (_I, [_P, C.POINTER(symnmf_schedule), C.POINTER(symnmf_report)]),
     "symnmf_leverage": (_I, [_P, _I, _P]),
     "symnmf_lvs_sample": (_I, [_P, _I, _I, _D, _I, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_float), _I,
                                _IP, _IP, _DP]),
@@ -99,6 +111,7 @@ _SIGS = {
     "symnmf_profile": (_I, [_P, _I]),
     "symnmf_profile_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
     "symnmf_profile_read_engine": (_I, [_P, _DP, C.POINTER(C.c_int64), _DP]),
+    "symnmf_profile_read_lvs": (_I, [_P, _DP, _DP, _DP, C.POINTER(C.c_int64)]),
     "symnmf_profile_standalone": (_I, [_I]),
     "symnmf_profile_standalone_read": (_I, [_DP, C.POINTER(C.c_int64), _DP, _DP]),
     "symnmf_batched_create": (_I, [C.POINTER(symnmf_problem), _I, _I, C.POINTER(symnmf_options), _P,
@@ -305,6 +318,17 @@ class Solver:
         self._chk(symnmf_pgncg(self.h, iters, source, s_max, obj.ctypes.data_as(_DP) if record else None))
         return obj[:iters] if record else None
 
+    def solve(self, method=SRC_LAI, rule=RULE_HALS, algo=0, l=None, q_max=10, ada_tol=1e-3, stop_tol=1e-4,
+              stop_count=4, max_iters=500, refine=True, max_refine=200, s_max=5):
+        """The experiments' schedule (symnmf_solve): Ada-RRF sketch, iterations to the stopping rule,
+        then Iterative Refinement on X; returns the report as a dict."""
+        sc = symnmf_schedule(method=method, algo=algo, rule=rule, l=l or (2 * self.k + 10), q_max=q_max,
+                             stop_count=stop_count, max_iters=max_iters, refine=1 if refine else 0,
+                             max_refine=max_refine, s_max=s_max, ada_tol=ada_tol, stop_tol=stop_tol)
+        rep = symnmf_report()
+        self._chk(symnmf_solve(self.h, C.byref(sc), C.byref(rep)))
+        return {f: getattr(rep, f) for f, _ in symnmf_report._fields_}
+
     # -- LvS
     def leverage(self, side):
         import torch
@@ -350,6 +374,12 @@ class Solver:
         t, n, f = C.c_double(), C.c_int64(), C.c_double()
         self._chk(symnmf_profile_read_engine(self.h, C.byref(t), C.byref(n), C.byref(f)))
         return t.value, n.value, f.value
+
+    def profile_read_lvs(self):
+        """(sampling ms, sampled-product ms, update ms, halves) of the LvS halves since the last read."""
+        a, b, c, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+        self._chk(symnmf_profile_read_lvs(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(n)))
+        return a.value, b.value, c.value, n.value
 
     # -- residual
     def residual(self, source=SRC_X, proj_grad=False):

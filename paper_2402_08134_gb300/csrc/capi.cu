@@ -137,6 +137,7 @@ static symnmf_status check_device_error(symnmf_t h) {
   unsigned e = 0;
   TRY(cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (e) TRY(cudaMemset(h->err, 0, sizeof(unsigned)));
+  if (e & (ERR_TIMEOUT | ERR_NAN)) h->eng_resume_ok = false;  // the engine's saved state is not trusted
   if (e & ERR_TIMEOUT) return fail(h, SYMNMF_ETIMEOUT, "a bounded device wait ran out");
   if (e & ERR_NOTSPD) return fail(h, SYMNMF_ENOTSPD, "Gram matrix is not positive definite");
   if (e & ERR_NAN) return fail(h, SYMNMF_ENAN, "non-finite value in a factor");
@@ -240,6 +241,8 @@ static const double* normx_for(symnmf_t h, int src) {
 
 // One half sweep: update F_upd (side 0: W, side 1: H) from the fixed factor.
 static symnmf_status half_sweep(symnmf_t h, int side, int src, int rule) {
+  h->fac_version++;
+  h->grams_fresh = true;  // the updated factor's Gram follows below, the other is current
   const int64_t n = h->n;
   const int k = h->k;
   float* Fu = side ? h->H : h->W;
@@ -294,6 +297,7 @@ static symnmf_status sweep_body(symnmf_t h, int src, int rule) {
 }
 
 static symnmf_status refresh_grams(symnmf_t h) {
+  h->grams_fresh = true;
   const int k = h->k;
   TRY(xcross(h->H, k, k, h->H, k, k, h->n, nullptr, nullptr, nullptr, nullptr, 0.0, h->Gd[0], h->Gf[0],
              h->ws, h->counters + 2, h->st));
@@ -435,6 +439,7 @@ extern "C" void symnmf_destroy(symnmf_t h) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
+  for (cudaEvent_t e : h->lprof_events) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFreeAsync(p, h->st);  // after the handle's work on its stream
   for (void* p : h->allocs_sync) cudaFree(p);
   delete h;
@@ -464,6 +469,7 @@ extern "C" symnmf_status symnmf_debug_wait_timeout(symnmf_t h, int64_t limit_ns)
 
 extern "C" symnmf_status symnmf_set_factors(symnmf_t h, const float* H0, const float* W0) {
   if (!h || !H0) return SYMNMF_EINVAL;
+  h->fac_version++;
   const size_t bytes = (size_t)h->n * h->k * sizeof(float);
   TRY(cudaMemcpyAsync(h->H, H0, bytes, cudaMemcpyDeviceToDevice, h->st));
   TRY(cudaMemcpyAsync(h->W, W0 ? W0 : H0, bytes, cudaMemcpyDeviceToDevice, h->st));
@@ -481,6 +487,7 @@ extern "C" symnmf_status symnmf_set_factors(symnmf_t h, const float* H0, const f
 
 extern "C" symnmf_status symnmf_init_random(symnmf_t h, int scaled) {
   if (!h) return SYMNMF_EINVAL;
+  h->fac_version++;
   TRY(philox_uniform(h->H, h->n, h->k, h->p.seed, scaled ? h->scal + S_MEAN : nullptr,
                      2.0 / sqrt((double)h->k), h->st));
   TRY(cudaMemcpyAsync(h->W, h->H, (size_t)h->n * h->k * 4, cudaMemcpyDeviceToDevice, h->st));
@@ -761,6 +768,9 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
   int done = 0;
   while (done < nsweeps) {
     const int chunk = (nsweeps - done) < OBJ_RING ? (nsweeps - done) : OBJ_RING;
+    // resume from the engine's saved state when nothing else touched W, H or the operator
+    const bool resume = h->eng_resume_ok && h->eng_fac_version == h->fac_version &&
+                        h->eng_lai_version == h->lai_version;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling && !h->capturing) {
       if (h->eprof_used == h->eprof_events.size()) {
@@ -772,11 +782,14 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
       }
       e0 = h->eprof_events[h->eprof_used].first;
       e1 = h->eprof_events[h->eprof_used].second;
-      h->eprof_flops[h->eprof_used] = lai_engine_flops(h->n, k, h->l, chunk);
+      h->eprof_flops[h->eprof_used] = lai_engine_flops(h->n, k, h->l, chunk, !resume);
       h->eprof_used++;
     }
     TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
-                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, e0, e1));
+                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, e0, e1, resume));
+    h->eng_resume_ok = true;
+    h->eng_fac_version = h->fac_version;
+    h->eng_lai_version = h->lai_version;
     if (obj_host) {
       TRY(cudaMemcpyAsync(obj_host + done, h->obj_ring, (size_t)chunk * sizeof(double), cudaMemcpyDeviceToHost,
                           h->st));
@@ -791,6 +804,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
     TRY(cudaMemcpyAsync(h->Gd[1], h->eng_G + k * k, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
     TRY(to_float_scaled(h->Gd[0], k, k, nullptr, h->Gf[0], h->st));
     TRY(to_float_scaled(h->Gd[1], k, k, nullptr, h->Gf[1], h->st));
+    h->grams_fresh = true;
   }
   return SYMNMF_OK;
 }
@@ -906,7 +920,9 @@ extern "C" symnmf_status symnmf_lvs_sample(symnmf_t h, int side, int iter, doubl
   return SYMNMF_OK;
 }
 
-static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule) {
+static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule, cudaEvent_t ev_products = nullptr) {
+  h->fac_version++;
+  h->grams_fresh = false;
   const int k = h->k;
   const int64_t n = h->n;
   const float* Ff = side ? h->W : h->H;
@@ -922,6 +938,7 @@ static symnmf_status lvs_update_dev(symnmf_t h, int side, int rule) {
   // G = F^T S^T S F
   TRY(xcross(Ff, k, k, Ff, k, k, h->sb.cap, h->sb.idx, h->sb.wt, h->sb.counts + 2, nullptr, 0.0, h->Gs_d,
              h->Gs_f, h->ws, h->counters + 5, h->st));
+  if (ev_products) TRY(cudaEventRecord(ev_products, h->st));
   if (rule == SYMNMF_RULE_HALS)
     TRY(hals_update(Fu, Ff, n, k, h->Gs_f, h->alpha, h->Y, k, nullptr, 0, nullptr, h->scal + S_PART,
                     h->ws, h->counters + 1, h->err, h->st));
@@ -947,15 +964,37 @@ extern "C" symnmf_status symnmf_lvs_update(symnmf_t h, int side, int rule) {
   return SYMNMF_OK;
 }
 
+// While profiling, the next LvS half's four events (before the leverage
+// scores, after the sample, after the sampled products, after the update).
+static symnmf_status lvs_events(symnmf_t h, cudaEvent_t* ev) {
+  if (!h->profiling || h->capturing) {
+    ev[0] = ev[1] = ev[2] = ev[3] = nullptr;
+    return SYMNMF_OK;
+  }
+  while (h->lprof_events.size() < 4 * (h->lprof_used + 1)) {
+    cudaEvent_t e;
+    TRY(cudaEventCreate(&e));
+    h->lprof_events.push_back(e);
+  }
+  for (int i = 0; i < 4; ++i) ev[i] = h->lprof_events[4 * h->lprof_used + i];
+  h->lprof_used++;
+  return SYMNMF_OK;
+}
+
 extern "C" symnmf_status symnmf_lvs_iterate(symnmf_t h, int iter0, int iters, double tau, int s, int rule) {
   if (!h || iters < 0 || s < 0) return SYMNMF_EINVAL;
   TRYS(check_lvs(h, rule));
   TRYS(ensure_sampler(h, s));
   for (int it = iter0; it < iter0 + iters; ++it) {
     for (int side = 0; side < 2; ++side) {
+      cudaEvent_t ev[4];
+      TRYS(lvs_events(h, ev));
+      if (ev[0]) TRY(cudaEventRecord(ev[0], h->st));
       TRYS(leverage_dev(h, side));
       TRYS(sample_dev(h, side, it, tau, s));
-      TRYS(lvs_update_dev(h, side, rule));
+      if (ev[1]) TRY(cudaEventRecord(ev[1], h->st));
+      TRYS(lvs_update_dev(h, side, rule, ev[2]));
+      if (ev[3]) TRY(cudaEventRecord(ev[3], h->st));
     }
   }
   TRYS(refresh_grams(h));
@@ -1024,6 +1063,8 @@ extern "C" symnmf_status symnmf_pgncg(symnmf_t h, int iters, int source, int s_m
       TRY(gn_update(h->cgP, h->cgY, nk, h->cgR, h->cgZ, h->cg_ws, h->counters + 7, cg, h->st));
       if (s + 1 < s_max) TRY(gn_dir(h->cgR, nk, h->cgP, cg, h->st));
     }
+    h->fac_version++;
+    h->grams_fresh = false;
     TRY(gn_project(h->cgZ, nk, h->H, h->W, h->err, h->st));
   }
   if (obj_host && iters > 0) {
@@ -1036,6 +1077,62 @@ extern "C" symnmf_status symnmf_pgncg(symnmf_t h, int iters, int source, int s_m
   return SYMNMF_OK;
 }
 
+// ------------------------------------------------------------ schedule
+
+// One iteration on `src` (a sweep, or a PGNCG iteration), returning the
+// normalized residual of that operator from the recorded objective.
+static symnmf_status schedule_step(symnmf_t h, const symnmf_schedule* sc, int src, double* nr) {
+  double obj = 0.0;
+  if (sc->algo == 1)
+    TRYS(symnmf_pgncg(h, 1, src, sc->s_max, &obj));
+  else
+    TRYS(symnmf_hals_sweep(h, 1, src, sc->rule, &obj));
+  double nx2 = 0.0;
+  TRY(cudaMemcpy(&nx2, normx_for(h, src), sizeof(double), cudaMemcpyDeviceToHost));
+  *nr = sqrt(fmax(obj, 0.0) / nx2);
+  return SYMNMF_OK;
+}
+
+// Iterations on `src` until the residual has fallen by less than stop_tol in
+// stop_count consecutive iterations, or `cap`.  Returns the iterations run.
+static symnmf_status schedule_phase(symnmf_t h, const symnmf_schedule* sc, int src, int cap, int* iters,
+                                    double* nr_last) {
+  double prev = 0.0, nr = 0.0;
+  int small = 0, t = 0;
+  while (t < cap) {
+    TRYS(schedule_step(h, sc, src, &nr));
+    ++t;
+    if (t > 1) small = (prev - nr < sc->stop_tol) ? small + 1 : 0;
+    prev = nr;
+    if (small >= sc->stop_count) break;
+  }
+  *iters = t;
+  *nr_last = nr;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_solve(symnmf_t h, const symnmf_schedule* sc, symnmf_report* rep) {
+  if (!h || !sc) return SYMNMF_EINVAL;
+  const int m = sc->method;
+  if (m != SYMNMF_SRC_X && m != SYMNMF_SRC_LAI && m != SYMNMF_SRC_COMP) return fail(h, SYMNMF_EINVAL, "method");
+  if (sc->algo == 1 && m == SYMNMF_SRC_COMP) return fail(h, SYMNMF_EINVAL, "PGNCG with X or LAI");
+  if (sc->stop_count < 1 || sc->max_iters < 0 || sc->max_refine < 0 || sc->q_max < 0)
+    return fail(h, SYMNMF_EINVAL, "schedule limits");
+  symnmf_report r{};
+  if (m != SYMNMF_SRC_X)
+    TRYS(symnmf_lai_sketch_ada(h, sc->l, sc->q_max, sc->ada_tol, nullptr, &r.checks, &r.passes, nullptr));
+  TRYS(schedule_phase(h, sc, m, sc->max_iters, &r.iters, &r.nr_phase));
+  const int truth = h->p.x_hi ? SYMNMF_SRC_XHI : SYMNMF_SRC_X;
+  if (sc->refine && m != SYMNMF_SRC_X) {
+    double nr_ir = 0.0;
+    TRYS(schedule_phase(h, sc, truth, sc->max_refine, &r.refine_iters, &nr_ir));
+  }
+  // PGNCG keeps W = H, so this is ||X - H H^T|| / ||X|| for it
+  TRYS(symnmf_residual(h, truth, &r.nr_final, nullptr, nullptr));
+  if (rep) *rep = r;
+  return SYMNMF_OK;
+}
+
 // -------------------------------------------------------------- residual
 
 extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double* surrogate,
@@ -1045,7 +1142,7 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
   TRYS(validate_sweep(h, source, SYMNMF_RULE_HALS));
   const int k = h->k;
   const int64_t n = h->n;
-  TRYS(refresh_grams(h));
+  if (!h->grams_fresh) TRYS(refresh_grams(h));
   auto apply_op = [&](const float* F, float* Yo) -> symnmf_status {
     if (source == SYMNMF_SRC_LAI) {
       TRY(xcross(h->U, h->l, h->l, F, k, k, n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf, h->ws,
@@ -1056,10 +1153,9 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
     return product(h, source, F, k, k, Yo, k);
   };
   TRYS(apply_op(h->H, h->Y));  // Y = X H
-  // part = (sum W .* XH, ||W - H||^2)
-  TRY(pair_reduce(h->W, h->Y, n * k, h->scal + S_PART2, h->ws, h->counters + 6, h->st));
-  TRY(pair_reduce(h->W, h->H, n * k, h->scal + S_PART3, h->ws, h->counters + 6, h->st));
-  TRY(objective(normx_for(h, source), h->Gd[1], h->Gd[0], k, h->scal + S_PART2, h->scal + S_ZERO,
+  // (sum W .* XH, ||W - H||^2) in one pass
+  TRY(resid_reduce(h->W, h->H, h->Y, n * k, h->scal + S_RES, h->ws, h->counters + 6, h->st));
+  TRY(objective(normx_for(h, source), h->Gd[1], h->Gd[0], k, h->scal + S_RES, h->scal + S_ZERO,
                 h->scal + S_OBJ, nullptr, 0, h->st));
   double pg2 = 0.0;
   if (proj_grad) {
@@ -1077,7 +1173,7 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
                                                 : hs[S_NORM2];
   pg2 = hs[S_PG];
   if (norm_resid) *norm_resid = sqrt(fmax(r2, 0.0) / nx2);
-  if (surrogate) *surrogate = r2 + h->alpha * hs[S_PART3 + 1];
+  if (surrogate) *surrogate = r2 + h->alpha * hs[S_RES + 1];
   if (proj_grad) *proj_grad = sqrt(pg2);
   return SYMNMF_OK;
 }
@@ -1146,7 +1242,7 @@ extern "C" symnmf_status symnmf_profile_standalone_read(double* total_ms, int64_
 extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, const float* row_scale,
                                          int64_t n, const float* F, int ldf, int N, float* Y, int ldy,
                                          int gemm, void* stream) {
-  if (!x || !F || !Y || n < 1 || N < 1 || N > 256 || ldx < n || ldf < N || ldy < N) return SYMNMF_EINVAL;
+  if (!x || !F || !Y || n < 1 || N < 1 || N > 512 || ldx < n || ldf < N || ldy < N) return SYMNMF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const bool tc = fmt == SYMNMF_X_DENSE_BF16 || fmt == SYMNMF_X_DENSE_FP8;
   if (tc && gemm == SYMNMF_GEMM_SIMT) return SYMNMF_EUNSUPPORTED;
@@ -1262,6 +1358,26 @@ extern "C" symnmf_status symnmf_profile(symnmf_t h, int enable) {
   h->profiling = enable != 0;
   h->prof_used = 0;
   h->eprof_used = 0;
+  h->lprof_used = 0;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_profile_read_lvs(symnmf_t h, double* sampling_ms, double* products_ms,
+                                                 double* update_ms, int64_t* halves) {
+  if (!h) return SYMNMF_EINVAL;
+  TRY(cudaStreamSynchronize(h->st));
+  double t[3] = {0.0, 0.0, 0.0};
+  for (size_t i = 0; i < h->lprof_used; ++i)
+    for (int b = 0; b < 3; ++b) {
+      float ms = 0.f;
+      TRY(cudaEventElapsedTime(&ms, h->lprof_events[4 * i + b], h->lprof_events[4 * i + b + 1]));
+      t[b] += ms;
+    }
+  if (sampling_ms) *sampling_ms = t[0];
+  if (products_ms) *products_ms = t[1];
+  if (update_ms) *update_ms = t[2];
+  if (halves) *halves = (int64_t)h->lprof_used;
+  h->lprof_used = 0;
   return SYMNMF_OK;
 }
 

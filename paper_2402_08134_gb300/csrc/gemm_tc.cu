@@ -13,10 +13,13 @@
 //                 HBM and needs the deeper buffering);
 //   warp 1      : TMEM allocator + MMA issuer (one thread);
 //   warps 2..5  : epilogue, tcgen05.ld of the accumulator -> FP32 partials.
-// Two TMEM accumulators alternate so that the epilogue of one accumulation
-// overlaps the MMAs of the next.  An accumulation covers at most 4 k blocks;
-// the epilogue adds the accumulations of a row tile in FP32 registers (round
-// to nearest), so the result carries no accumulator drift over long K.
+// Up to 128 columns, four TMEM accumulators alternate so that the epilogue of
+// one accumulation overlaps the MMAs of the next ones; an accumulation covers
+// at most 8 k blocks and the epilogue adds a row tile's accumulations in FP32
+// registers (round to nearest), which keeps the tensor core's per-MMA
+// accumulation drift (~2e-8 relative, low) from building up over long K.
+// Wider products (256 columns on 256-row tiles, 512 columns) fill TMEM with
+// one accumulator per segment and keep that drift (~6e-5 at K = 20000).
 //
 // Work split (stream-K): the (row tile, k block) iteration space is cut into
 // gridDim.x equal contiguous ranges, one per CTA, so every SM streams the
@@ -36,29 +39,42 @@
 #include "kernels.h"
 #include "tc_common.cuh"
 
+#ifndef XF_TC_CHUNK
+#define XF_TC_CHUNK 8  // k blocks per TMEM accumulation (128-row tiles)
+#endif
+
 namespace symnmf {
 
 constexpr int XF_THREADS = 224;  // warps 0..6: A producer, MMA, 4 epilogue warps, B producer
 
 // M2: a CTA's row tile is 256 rows (two 128-row MMA halves sharing every F
 // stage, accumulators in TMEM columns [0, BN) and [BN, 2 BN), one buffer);
-// otherwise 128 rows with two alternating accumulators.
+// otherwise 128 rows.  BN = 512 (128 rows): each k step issues two N = 256
+// MMAs into TMEM columns [0, 256) and [256, 512), one buffer; each F stage is
+// two 256-row TMA boxes.
 template <int BN, bool M2 = false>
 struct TcCfg {
   static constexpr int BM = M2 ? 2 * TC_BM : TC_BM;
+  static constexpr bool WIDE = BN > 256;
+  static constexpr int MMA_N = WIDE ? 256 : BN;     // columns per MMA
+  static constexpr int NB_MMA = BN / MMA_N;         // MMAs per k step and row half
+  static constexpr bool REGACC = !M2 && BN <= 128;  // epilogue adds accumulations in registers
   static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
-  static constexpr int B_STAGES = M2 ? 3 : 4;
+  static constexpr int B_STAGES = WIDE ? 2 : M2 ? 3 : 4;
   static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
-  static constexpr int NBUF = M2 ? 1 : 2;  // accumulator buffers in TMEM
+  // accumulator buffers in TMEM: four alternate, so that the epilogue's drains
+  // of short accumulations never hold up the MMAs
+  static constexpr int NBUF = REGACC ? 4 : 1;
   // k blocks accumulated in TMEM before the epilogue adds them into FP32
   // registers (round to nearest): the tensor core's accumulation drifts low by
   // a fraction of an FP32 ulp per MMA, which over a whole 20000-long K range
   // biased X F by ~7e-5 relative.  256-row tiles keep one accumulation per
   // segment (their single TMEM buffer has no room to alternate).
-  static constexpr int64_t CHUNK = M2 ? (int64_t)1 << 40 : 4;
-  static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
+  static constexpr int64_t CHUNK = REGACC ? XF_TC_CHUNK : (int64_t)1 << 40;
+  static constexpr uint32_t TMEM_COLS = M2 ? 2 * BN : (NBUF * BN < 32 ? 32 : NBUF * BN);
+  static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
   static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
 };
 
@@ -72,7 +88,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
   constexpr int SA = C::A_STAGES, SB = C::B_STAGES;
   constexpr int KSTEPS = TC_ROW_BYTES / 32;  // 32 bytes of K per MMA (16 bf16 / 32 e4m3)
   constexpr int KELEMS = FP8 ? 128 : 64;     // elements of K per k block
-  constexpr uint32_t IDESC = make_idesc<FP8>(TC_BM, BN);
+  constexpr uint32_t IDESC = make_idesc<FP8>(TC_BM, C::MMA_N);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -83,8 +99,8 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
   uint64_t* fullB = emptyA + SA;
   uint64_t* emptyB = fullB + SB;
   uint64_t* tfull = emptyB + SB;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* done = tempty + 2;
+  uint64_t* tempty = tfull + 4;
+  uint64_t* done = tempty + 4;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -101,7 +117,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
       mbar_init(&fullB[s], 1);
       mbar_init(&emptyB[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < 4; ++a) {
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 4);
     }
@@ -149,7 +165,10 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
                         tile * BM + h * TC_BM, &fullR[stage]);
         } else {
           mbar_expect_tx(&fullR[stage], C::B_BYTES);
-          tma_load_2d(sB + stage * C::B_BYTES, &tmB, kb * KELEMS, 0, &fullR[stage]);
+#pragma unroll
+          for (int j = 0; j < C::NB_MMA; ++j)
+            tma_load_2d(sB + stage * C::B_BYTES + j * C::MMA_N * TC_ROW_BYTES, &tmB, kb * KELEMS, j * C::MMA_N,
+                        &fullR[stage]);
         }
         issued_mask |= 1u << stage;
         last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
@@ -198,8 +217,12 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
           for (int h = 0; h < BM / TC_BM; ++h)
 #pragma unroll
             for (int ks = 0; ks < KSTEPS; ++ks)
-              umma<FP8>(d + (uint32_t)(h * BN), sw128_desc(a0 + h * TC_BM * TC_ROW_BYTES + ks * 32),
-                        sw128_desc(b0 + ks * 32), IDESC, (it > seg_begin || ks > 0) ? 1u : 0u);
+#pragma unroll
+              for (int j = 0; j < C::NB_MMA; ++j)
+                umma<FP8>(d + (uint32_t)(h * BN + j * C::MMA_N),
+                          sw128_desc(a0 + h * TC_BM * TC_ROW_BYTES + ks * 32),
+                          sw128_desc(b0 + j * C::MMA_N * TC_ROW_BYTES + ks * 32), IDESC,
+                          (it > seg_begin || ks > 0) ? 1u : 0u);
           umma_commit(&emptyA[sa]);
           umma_commit(&emptyB[sb]);
           if (++sa == SA) {
@@ -229,7 +252,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
     const int ew = warp & 3;
     int seg = 0;
     int64_t it = it0;
-    if constexpr (!M2) {
+    if constexpr (C::REGACC) {
       // one thread per row of the 128-row tile: the chunks' accumulators are
       // added in registers (round to nearest) and the segment's sum written once
       int dr = 0;
@@ -271,7 +294,7 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
         ++seg;
       }
     }
-    while (M2 && it < it1) {
+    while (!C::REGACC && it < it1) {
       const int64_t tile = it / kblocks;
       const int64_t seg_end = min(it1, (tile + 1) * kblocks);
       const int a = seg % NBUF;
@@ -381,7 +404,8 @@ int tc_block_n(int N) {
   if (N <= 32) return 32;
   if (N <= 64) return 64;
   if (N <= 128) return 128;
-  return 256;
+  if (N <= 256) return 256;
+  return 512;
 }
 
 struct TcPlan {
@@ -391,7 +415,7 @@ struct TcPlan {
 
 // Row tiles of 256 (two MMA halves sharing each F stage) for the widest
 // products, where F's traffic from L2 would otherwise limit the tensor rate.
-static bool tc_m2(int N) { return N > 128; }
+static bool tc_m2(int N) { return N > 128 && N <= 256; }
 
 static TcPlan tc_plan(int64_t n, bool fp8, int bm = TC_BM) {
   TcPlan p;
@@ -504,7 +528,7 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   const bool fp8 = fmt == 3;
   if (!fp8 && fmt != 2) return cudaErrorInvalidValue;
   const int BN = tc_block_n(N);
-  if (N > 256) return cudaErrorInvalidValue;
+  if (N > 512) return cudaErrorInvalidValue;
   const size_t es = fp8 ? 1 : 2;
   // TMA: 16-byte aligned bases and row pitches
   if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
@@ -516,7 +540,8 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   const uint32_t kel = fp8 ? 128 : 64;
   if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)n, (uint64_t)ldx * es, kel, TC_BM))
     return cudaErrorInvalidValue;
-  if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel, (uint32_t)BN))
+  if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel,
+                   (uint32_t)(BN > 256 ? 256 : BN)))
     return cudaErrorInvalidValue;
   cudaError_t e;
   if (ev_begin) cudaEventRecord(ev_begin, st);
@@ -525,14 +550,16 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
       case 32: e = launch_tc<32, true>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, true>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<256, true, true>(ma, mb, p, ws, err, st); break;
+      case 256: e = launch_tc<256, true, true>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<512, true>(ma, mb, p, ws, err, st); break;
     }
   } else {
     switch (BN) {
       case 32: e = launch_tc<32, false>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, false>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, false>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<256, false, true>(ma, mb, p, ws, err, st); break;
+      case 256: e = launch_tc<256, false, true>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc<512, false>(ma, mb, p, ws, err, st); break;
     }
   }
   if (ev_end) cudaEventRecord(ev_end, st);

@@ -30,7 +30,8 @@ enum {
   S_ADA = 20,       // 2 slots: ||B||_F^2 of the adaptive range finder's check
   S_COMP_NORM2 = 22,  // 2 slots: ||Q^T X||_F^2 of the compressed problem
   S_CG = 24,        // GN_COUNT slots: scalars of the PGNCG conjugate-gradient loop
-  S_COUNT = 32
+  S_RES = 32,       // 2 slots: sum W .* (X H), ||W - H||^2 of a residual evaluation
+  S_COUNT = 40
 };
 constexpr int OBJ_RING = 4096;
 
@@ -99,6 +100,14 @@ struct symnmf_ctx {
     uint64_t nkernels = 0;
   } graphs[6];
   bool capturing = false;
+  // factor bookkeeping: fac_version counts writes of W / H by anything but the
+  // LAI engine; the engine may resume from its own saved state (skipping its
+  // prologue) while nothing else has written the factors or the operator since
+  uint64_t fac_version = 0;
+  bool eng_resume_ok = false;
+  uint64_t eng_fac_version = 0;
+  int eng_lai_version = -1;
+  bool grams_fresh = false;  // Gd / Gf hold H^T H and W^T W of the current factors
   cudaStream_t cap_st = nullptr;
 
   // live timing of the tensor-core product kernel (eager calls only)
@@ -106,6 +115,8 @@ struct symnmf_ctx {
   size_t prof_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   std::vector<double> prof_bytes;
+  size_t lprof_used = 0;  // LvS halves timed while profiling: 4 events each
+  std::vector<cudaEvent_t> lprof_events;
   size_t eprof_used = 0;  // LAI sweep engine launches timed while profiling
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eprof_events;
   std::vector<double> eprof_flops;

@@ -87,6 +87,9 @@ cudaError_t objective(const double* normX2, const double* Ga, const double* Gb, 
 // out[0] = sum a .* b, out[1] = sum (a - b)^2 (FP64); ws >= 2 * 2 * num_sms() doubles.
 cudaError_t pair_reduce(const float* a, const float* b, int64_t count, double* out, double* ws,
                         unsigned* counter, cudaStream_t st);
+// out[0] = sum w .* y, out[1] = sum (w - h)^2 (FP64; ws >= 2 * 2 * num_sms() doubles).
+cudaError_t resid_reduce(const float* w, const float* h, const float* y, int64_t count, double* out, double* ws,
+                         unsigned* counter, cudaStream_t st);
 cudaError_t sumsq(const double* v, int l, double* out, cudaStream_t st);
 // out = ||U diag(lam) U^T||_F^2 = sum_ij lam_i lam_j Gu_ij^2 with Gu = U^T U (l x l FP64).
 cudaError_t lai_norm2(const double* Gu, const double* lam, int l, double* out, cudaStream_t st);
@@ -149,16 +152,18 @@ cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, ui
 // ------------------------------------------------------------- LAI engine
 // All `nsweeps` LAI-HALS sweeps in one cooperative launch (see lai_engine.cu);
 // `allow_resident` lets the CTAs keep their rows in shared memory when they fit.
+// `resume`: W, H and the workspace are as the previous launch on this
+// workspace left them, so its saved state replaces the prologue.
 size_t lai_engine_ws_bytes(int l, int k, int obj_cap);
 // ev_begin / ev_end (optional) are recorded right around the kernel launch.
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
                        double* Gout, unsigned* err, bool allow_resident, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, bool resume = false);
 // Algorithmic FLOPs of one engine launch: per half sweep n (l k [Y = U M] +
 // k^2 [column updates] + l k [U^T F] + k (k + 1) / 2 [F^T F]) FMAs, plus the
-// prologue's n (l k + k (k + 1) / 2); two FLOPs per FMA.
-double lai_engine_flops(int64_t n, int k, int l, int nsweeps);
+// prologue's n (l k + k (k + 1) / 2) (not run by a resumed launch); two FLOPs per FMA.
+double lai_engine_flops(int64_t n, int k, int l, int nsweeps, bool prologue = true);
 
 // -------------------------------------------------------------- CholeskyQR3
 // Shifted CholeskyQR3 of S (n x l, l <= 96) in place; T is n x l scratch for

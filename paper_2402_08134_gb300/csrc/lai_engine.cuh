@@ -12,13 +12,14 @@
 //   per half sweep
 //     1. each CTA updates its rows (Y = U M for its rows, then per row the
 //        columns in order, each using the ones already updated) and writes
-//        one FP32 record of its partial sums over its rows: U^T F_upd,
+//        one FP32 record (its row groups added) of its partial sums over its rows: U^T F_upd,
 //        F_upd^T F_upd (upper 4x4 tiles; FMA sums over four rows folded into
 //        Kahan-compensated totals, each rounded once), and (as hi/lo float
 //        pairs of FP64 sums) F_upd . Y and ||F_upd - F_fix||^2;
 //     2. grid barrier;
 //     3. CTA c sums slice c of the entries over all records in double-float
-//        (Dekker's two-sum; fixed order: deterministic) and writes the FP64
+//        (Dekker's two-sum; a warp per float4 column, lanes over records, a
+//        fixed shuffle tree: deterministic) and writes the FP64
 //        sums, plus the next half's state in FP32 -- lambda-scaled M, G and
 //        1 / (G_ii + alpha) laid out as the CTAs hold them in shared memory --
 //        and, after the H half, its share of the surrogate objective (trace
@@ -81,6 +82,7 @@ struct LaiArgs {
   int tile_rows;         // streamed: rows per tile; resident: rows per CTA padded to 4 (RP)
   int gp;                // G held as gp x gp (gp = KMAX of the kernel), zero padded
   int pitch;             // resident: column pitch (RP padded to 8)
+  int resume;            // 1: the H-side state saved by the previous launch is current (no prologue)
 };
 
 // Final sums: l*k entries of U^T F, k*k of F^T F, then tr, dd.
@@ -182,30 +184,56 @@ __device__ __forceinline__ void le_settle(float (&acc)[3][16], const float (&cmp
     for (int e = 0; e < 16; ++e) acc[t][e] -= cmp[t][e];
 }
 
-// Write this CTA's records (one per row group; coalesced float4 stores of the
-// tiles) and the CTA's tr, dd (double-float, reduced over the block with one
-// barrier) into the first record; the other records' tr, dd slots get zeros.
+// Write this CTA's record: the row groups' tile sums (Kahan-settled FP32) are
+// staged in shared memory and added in row-group order, then stored as float4
+// runs; the CTA's tr, dd (double-float, reduced over the block) fill the last
+// four floats.  One record per CTA.
 __device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, const float (&acc)[3][16],
                                           float* red, float2 trv, float2 ddv) {
   const int EP = le_rec_entries(a.l, a.k);
-  float* rec0 = a.part + (size_t)blockIdx.x * tl.RG * EP;
-  for (int t = 0; t < tl.TPT; ++t) {
-    const int tile = le_tile_of(tl, t);
-    if (tile < tl.T && tl.my_rg < tl.RG) {
-      float4* rec4 = reinterpret_cast<float4*>(rec0 + (size_t)tl.my_rg * EP);
+  float* rec = a.part + (size_t)blockIdx.x * EP;
+  if (tl.RG == 1) {
+    for (int t = 0; t < tl.TPT; ++t) {
+      const int tile = le_tile_of(tl, t);
+      if (tile < tl.T && tl.my_rg == 0) {  // threads past the row groups hold no sums
+        float4* rec4 = reinterpret_cast<float4*>(rec);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float v[4];
+        for (int u = 0; u < 4; ++u) {
+          float v[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          v[e] = 0.f;
+          for (int e = 0; e < 4; ++e) {
+            v[e] = 0.f;
 #pragma unroll
-          for (int w = 0; w < 3; ++w)
-            if (w == t) v[e] = acc[w][4 * u + e];
+            for (int w = 0; w < 3; ++w)
+              if (w == t) v[e] = acc[w][4 * u + e];
+          }
+          rec4[tile * 4 + u] = make_float4(v[0], v[1], v[2], v[3]);
         }
-        rec4[tile * 4 + u] = make_float4(v[0], v[1], v[2], v[3]);
       }
     }
+  } else {
+    // TPT == 1: thread (rg, tile) holds acc[0]; RG * T * 16 <= 16 * LE_THREADS floats fit red
+    const int tile = le_tile_of(tl, 0);
+    if (tile < tl.T && tl.my_rg < tl.RG) {
+      float4* dst = reinterpret_cast<float4*>(red + ((size_t)tl.my_rg * tl.T + tile) * 16);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dst[u] = make_float4(acc[0][4 * u], acc[0][4 * u + 1], acc[0][4 * u + 2],
+                                                       acc[0][4 * u + 3]);
+    }
+    __syncthreads();
+    const int nq = tl.T * 4;  // float4 runs of the record's tiles
+    for (int q = threadIdx.x; q < nq; q += LE_THREADS) {
+      float4 s4 = reinterpret_cast<const float4*>(red)[q];
+      for (int g = 1; g < tl.RG; ++g) {
+        const float4 v = reinterpret_cast<const float4*>(red)[(size_t)g * nq + q];
+        s4.x += v.x;
+        s4.y += v.y;
+        s4.z += v.z;
+        s4.w += v.w;
+      }
+      reinterpret_cast<float4*>(rec)[q] = s4;
+    }
+    __syncthreads();  // red is reused below
   }
   // tr, dd: warp xor trees, then one barrier and warp 0
 #pragma unroll
@@ -230,142 +258,102 @@ __device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, c
       df_add(th, tl2, __shfl_xor_sync(0xffffffffu, th, o), __shfl_xor_sync(0xffffffffu, tl2, o));
       df_add(dh, dl, __shfl_xor_sync(0xffffffffu, dh, o), __shfl_xor_sync(0xffffffffu, dl, o));
     }
-    if (lane < tl.RG) {
-      float* r2 = rec0 + (size_t)lane * EP + EP - 4;
-      r2[0] = lane == 0 ? th : 0.f;
-      r2[1] = lane == 0 ? tl2 : 0.f;
-      r2[2] = lane == 0 ? dh : 0.f;
-      r2[3] = lane == 0 ? dl : 0.f;
-    }
+    if (lane == 0) reinterpret_cast<float4*>(rec + EP - 4)[0] = make_float4(th, tl2, dh, dl);
   }
   __syncthreads();  // red is reused by the caller
 }
 
-// Sliced reduction of all records.  CTA c owns a contiguous run of record
-// positions; its threads read them coalesced (consecutive threads, consecutive
-// positions of one record), each thread summing every S-th record in
-// double-float, and the S partial sums of a position are then added in a fixed
-// order (deterministic).  Each position is mapped back to its entry: the FP64
-// sums go to fin[side] (both (i, j) and (j, i) for F^T F), the FP32 state of the
-// next half to state[side], and after the H half of sweep t >= 0 this CTA's
-// objective share to objp[t].
-// Records are read as float4 runs, LE_BATCH per thread in flight; a chunk of
-// at most LE_CHUNK positions is reduced at a time.  red holds the group sums
-// (2 floats per position and group: at most 2 LE_THREADS float4s) and, from
-// LE_STAGE on, the chunk's final (hi, lo) pairs.
+// Sliced reduction of all records (one per CTA).  CTA c owns a contiguous run
+// of record positions (whole float4 columns); each warp reduces one column at
+// a time: lane j sums the column's float4 in records j, j + 32, ... in
+// double-float (all its loads in flight together), then a fixed xor tree over
+// the lanes adds the 32 partial sums (deterministic).  Each position is mapped
+// back to its entry: the FP64 sums go to fin[side] (both (i, j) and (j, i) for
+// F^T F), the FP32 state of the next half to state[side], and after the H half
+// of sweep t >= 0 this CTA's objective share to objp[t].
 constexpr int LE_BATCH = 8;
-constexpr int LE_CHUNK = 4 * 64;
-constexpr int LE_STAGE = 8 * LE_THREADS;
 
 __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int t, float* red, double* shd) {
+  (void)red;
   const int k = a.k, l = a.l, k4 = (k + 3) & ~3, gp = a.gp;
   const int E = le_entries(l, k), EP = le_rec_entries(l, k), SL = le_state_floats(l, k, gp);
   const int lk = l * k, kt = k4 / 4, tm = (((l + 3) & ~3) / 4) * kt;
-  const unsigned nrec = gridDim.x * le_row_groups(l, k);
+  const unsigned nrec = gridDim.x;
   double* fin = a.fin + side * E;
   float* st = a.state + side * SL;
-  // positions per CTA, a multiple of 4: float4 runs of a record, and the hi/lo
-  // pairs of tr and dd (at EP - 4, EP - 2; EP is a multiple of 4) never straddle two CTAs
+  // positions per CTA, a multiple of 4: the float4 columns and the hi/lo pairs of
+  // tr and dd (the last column, EP a multiple of 4) never straddle two CTAs
   const int per = ((EP + gridDim.x - 1) / gridDim.x + 3) & ~3;
   const int c0 = blockIdx.x * per, c1 = min(EP, c0 + per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double share = 0.0;
-  for (int i0 = c0; i0 < c1; i0 += LE_CHUNK) {  // chunks of at most LE_CHUNK positions
-    const int np = min(LE_CHUNK, c1 - i0);
-    const int nc = (np + 3) / 4;        // float4 columns of the chunk
-    const int S = LE_THREADS / nc;      // record groups (>= 4)
-    const int col = threadIdx.x % nc, g = threadIdx.x / nc;
-    // group g sums records g, g + S, ... of its column in double-float
-    if (g < S) {
-      float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* src = a.part + i0 + 4 * col;  // i0 + 4 col < EP: the run stays in its record
-      for (unsigned q0 = g; q0 < nrec; q0 += (unsigned)S * LE_BATCH) {
-        float4 v[LE_BATCH];
+  for (int col = c0 + 4 * wid; col < c1; col += 4 * (LE_THREADS / 32)) {
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* src = a.part + col;
+    for (unsigned q0 = lane; q0 < nrec; q0 += 32u * LE_BATCH) {
+      float4 v[LE_BATCH];
 #pragma unroll
-        for (int u = 0; u < LE_BATCH; ++u) {
-          const unsigned q = q0 + (unsigned)S * u;
-          v[u] = q < nrec ? __ldcg(reinterpret_cast<const float4*>(src + (size_t)q * EP))
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+      for (int u = 0; u < LE_BATCH; ++u) {
+        const unsigned q = q0 + 32u * u;
+        v[u] = q < nrec ? __ldcg(reinterpret_cast<const float4*>(src + (size_t)q * EP))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
-        for (int u = 0; u < LE_BATCH; ++u) {
-          df_add(hi[0], lo[0], v[u].x, 0.f);
-          df_add(hi[1], lo[1], v[u].y, 0.f);
-          df_add(hi[2], lo[2], v[u].z, 0.f);
-          df_add(hi[3], lo[3], v[u].w, 0.f);
-        }
+      for (int u = 0; u < LE_BATCH; ++u) {
+        df_add(hi[0], lo[0], v[u].x, 0.f);
+        df_add(hi[1], lo[1], v[u].y, 0.f);
+        df_add(hi[2], lo[2], v[u].z, 0.f);
+        df_add(hi[3], lo[3], v[u].w, 0.f);
       }
-      float4* r4 = reinterpret_cast<float4*>(red) + 2 * (g * nc + col);
-      r4[0] = make_float4(hi[0], lo[0], hi[1], lo[1]);
-      r4[1] = make_float4(hi[2], lo[2], hi[3], lo[3]);
     }
-    __syncthreads();
-    // the S group sums of each column by a fixed tree (deterministic)
-    for (int sg = 1; sg < S; sg <<= 1) {
-      if (g < S && (g & (2 * sg - 1)) == 0 && g + sg < S) {
-        float4* r4 = reinterpret_cast<float4*>(red) + 2 * (g * nc + col);
-        const float4* o4 = reinterpret_cast<const float4*>(red) + 2 * ((g + sg) * nc + col);
-        float4 x0 = r4[0], x1 = r4[1];
-        const float4 y0 = o4[0], y1 = o4[1];
-        df_add(x0.x, x0.y, y0.x, y0.y);
-        df_add(x0.z, x0.w, y0.z, y0.w);
-        df_add(x1.x, x1.y, y1.x, y1.y);
-        df_add(x1.z, x1.w, y1.z, y1.w);
-        r4[0] = x0;
-        r4[1] = x1;
-      }
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        df_add(hi[e], lo[e], __shfl_xor_sync(0xffffffffu, hi[e], o), __shfl_xor_sync(0xffffffffu, lo[e], o));
+    if (lane != 0) continue;
+    if (col == EP - 4) {
+      // tr and dd: hi/lo pairs of double-float sums
+      const double tr = (double)hi[0] + (double)lo[0] + (double)hi[1] + (double)lo[1];
+      const double dd = (double)hi[2] + (double)lo[2] + (double)hi[3] + (double)lo[3];
+      fin[lk + k * k] = tr;
+      fin[lk + k * k + 1] = dd;
+      if (side == 1 && t >= 0) share += -2.0 * tr + a.alpha_d * dd;
+      continue;
     }
-    const int idx = i0 + (int)threadIdx.x;
-    if ((int)threadIdx.x < np) {
-      // group 0 holds column c's four sums as (hi, lo) pairs: position 4 c + e at red[8 c + 2 e]
-      const float h = red[2 * threadIdx.x], o = red[2 * threadIdx.x + 1];
-      red[LE_STAGE + 2 * threadIdx.x] = h;  // stage for the pairs of tr, dd
-      red[LE_STAGE + 2 * threadIdx.x + 1] = o;
-      const double v = (double)h + (double)o;
-      if (idx < EP - 4) {
-        const int tile = idx >> 4, p = (idx >> 2) & 3, q = idx & 3;
-        if (tile < tm) {
-          const int i = 4 * (tile / kt) + p, j = 4 * (tile % kt) + q;
-          if (i < l && j < k) {
-            fin[i * k + j] = v;
-            st[i * k4 + j] = (float)(a.lam[i] * v);
-            // the H half's rows used M~ = fl32(lambda U^T W), rounded once and shared by
-            // every row, so tr(H^T U M~) misses the exact tr by sum (U^T H) .* (M~ - M):
-            // added back here, where U^T H (this sum, v) and U^T W (fin[0]) are in FP64
-            if (side == 1 && t >= 0) {
-              const double m = a.lam[i] * __ldcg(a.fin + i * k + j);
-              share += 2.0 * v * ((double)(float)m - m);
-            }
-          }
-        } else {
-          int bi, bj;
-          le_tri(tile - tm, kt, bi, bj);
-          const int i = 4 * bi + p, j = 4 * bj + q;
-          if (i < k && j < k) {
-            fin[lk + i * k + j] = v;
-            fin[lk + j * k + i] = v;
-            st[l * k4 + i * gp + j] = (float)v;
-            st[l * k4 + j * gp + i] = (float)v;
-            if (i == j) st[l * k4 + gp * gp + i] = 1.0f / ((float)v + a.alpha);
-            // (W^T W)_ij (H^T H)_ij over all (i, j): an off-diagonal tile holds each pair once
-            if (side == 1 && t >= 0) share += (bi == bj ? 1.0 : 2.0) * __ldcg(a.fin + lk + i * k + j) * v;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = col + e;
+      const double v = (double)hi[e] + (double)lo[e];
+      const int tile = idx >> 4, p = (idx >> 2) & 3, q = idx & 3;
+      if (tile < tm) {
+        const int i = 4 * (tile / kt) + p, j = 4 * (tile % kt) + q;
+        if (i < l && j < k) {
+          fin[i * k + j] = v;
+          st[i * k4 + j] = (float)(a.lam[i] * v);
+          // the H half's rows used M~ = fl32(lambda U^T W), rounded once and shared by
+          // every row, so tr(H^T U M~) misses the exact tr by sum (U^T H) .* (M~ - M):
+          // added back here, where U^T H (this sum, v) and U^T W (fin[0]) are in FP64
+          if (side == 1 && t >= 0) {
+            const double m = a.lam[i] * __ldcg(a.fin + i * k + j);
+            share += 2.0 * v * ((double)(float)m - m);
           }
         }
+      } else {
+        int bi, bj;
+        le_tri(tile - tm, kt, bi, bj);
+        const int i = 4 * bi + p, j = 4 * bj + q;
+        if (i < k && j < k) {
+          fin[lk + i * k + j] = v;
+          fin[lk + j * k + i] = v;
+          st[l * k4 + i * gp + j] = (float)v;
+          st[l * k4 + j * gp + i] = (float)v;
+          if (i == j) st[l * k4 + gp * gp + i] = 1.0f / ((float)v + a.alpha);
+          // (W^T W)_ij (H^T H)_ij over all (i, j): an off-diagonal tile holds each pair once
+          if (side == 1 && t >= 0) share += (bi == bj ? 1.0 : 2.0) * __ldcg(a.fin + lk + i * k + j) * v;
+        }
       }
     }
-    __syncthreads();
-    // tr and dd: hi/lo pairs at positions EP - 4 .. EP - 1
-    if (threadIdx.x < np && (idx == EP - 4 || idx == EP - 2)) {
-      float h = red[LE_STAGE + 2 * threadIdx.x], o = red[LE_STAGE + 2 * threadIdx.x + 1];
-      if (threadIdx.x + 1 < np) {
-        df_add(h, o, red[LE_STAGE + 2 * threadIdx.x + 2], red[LE_STAGE + 2 * threadIdx.x + 3]);
-        const double v = (double)h + (double)o;
-        const int e = lk + k * k + (idx == EP - 4 ? 0 : 1);
-        fin[e] = v;
-        if (side == 1 && t >= 0) share += (idx == EP - 4) ? -2.0 * v : a.alpha_d * v;  // -2 tr, + alpha dd
-      }
-    }
-    __syncthreads();
   }
   if (side == 1 && t >= 0) {
     share = block_sum(share, shd);
@@ -487,15 +475,18 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
     }
   };
 
-  // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
-  le_clear(acc, cmp);
-  accumulate(Ht);
-  le_settle(acc, cmp);
-  le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+  // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H),
+  // unless the previous launch saved it
   unsigned epoch = 0;
-  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-  le_reduce_slice(a, 1, -1, red, shd);
-  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  if (!a.resume) {
+    le_clear(acc, cmp);
+    accumulate(Ht);
+    le_settle(acc, cmp);
+    le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+    le_reduce_slice(a, 1, -1, red, shd);
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  }
   le_load_state(a, 1, Ms);
 
   const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
@@ -657,21 +648,24 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
     }
   };
 
-  // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H)
-  le_clear(acc, cmp);
-  for (int64_t b = r0; b < r1; b += TR) {
-    const int rows = (int)min((int64_t)TR, r1 - b);
-    stage(b, rows, nullptr, a.H);
-    __syncthreads();
-    accumulate(rows);
-    __syncthreads();
-  }
-  le_settle(acc, cmp);
-  le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+  // prologue: state of the H side (the W-update uses M = Lambda U^T H, G = H^T H),
+  // unless the previous launch saved it
   unsigned epoch = 0;
-  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-  le_reduce_slice(a, 1, -1, red, shd);
-  if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  if (!a.resume) {
+    le_clear(acc, cmp);
+    for (int64_t b = r0; b < r1; b += TR) {
+      const int rows = (int)min((int64_t)TR, r1 - b);
+      stage(b, rows, nullptr, a.H);
+      __syncthreads();
+      accumulate(rows);
+      __syncthreads();
+    }
+    le_settle(acc, cmp);
+    le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+    le_reduce_slice(a, 1, -1, red, shd);
+    if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
+  }
   le_load_state(a, 1, Ms);
 
   const float4* Ms4 = reinterpret_cast<const float4*>(Ms);

@@ -599,6 +599,38 @@ __global__ void pair_reduce_kernel(const float* __restrict__ a, const float* __r
   }
 }
 
+// out[0] = sum w .* y, out[1] = sum (w - h)^2 in one pass (the residual's two sums).
+__global__ void resid_reduce_kernel(const float* __restrict__ w, const float* __restrict__ h,
+                                    const float* __restrict__ y, int64_t count, double* out, double* ws,
+                                    unsigned* counter) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[t];
+    const double d = x - (double)h[t];
+    s0 += x * (double)y[t];
+    s1 += d * d;
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    ws[2 * blockIdx.x] = s0;
+    ws[2 * blockIdx.x + 1] = s1;
+  }
+  if (last_block<1>(counter)) {
+    reduce_partials(ws, 2, 2, gridDim.x, out, sh);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+cudaError_t resid_reduce(const float* w, const float* h, const float* y, int64_t count, double* out, double* ws,
+                         unsigned* counter, cudaStream_t st) {
+  resid_reduce_kernel<<<num_sms() * 2, 256, 0, st>>>(w, h, y, count, out, ws, counter);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t pair_reduce(const float* a, const float* b, int64_t count, double* out, double* ws,
                         unsigned* counter, cudaStream_t st) {
   pair_reduce_kernel<<<num_sms() * 2, 256, 0, st>>>(a, b, count, out, ws, counter);

@@ -186,3 +186,29 @@ def test_compressed_sweeps_match_oracle(S, rule):
     # not a residual source
     with pytest.raises(S.SymNMFError):
         s.residual(S.SRC_COMP)
+
+
+def test_paper_schedule_matches_oracle(S):
+    # the experiments' schedule: Ada-RRF (1e-3), LAI-HALS to the 1e-4 x 4 stopping rule, then
+    # Iterative Refinement on X with the same rule, against the oracle's run of the same schedule
+    from oracle import philox
+
+    X, _ = _gmm_kernel(2000, 10, 6, seed=18)
+    n, k, l, seed = 2000, 6, 22, 9
+    Hi = (uniform_factor(n, k, seed=19) * O.init_scale(X, k)).astype(np.float32).astype(np.float64)
+    s = S.Solver(t32(X), k, max_width=l, seed=seed)
+    s.set_factors(t32(Hi))
+    got = s.solve(method=S.SRC_LAI, l=l, q_max=8, max_iters=300, max_refine=300)
+    ref = O.lai_schedule(X, philox.philox_gaussian(n, l, seed), Hi, O.default_alpha(X), q_max=8, max_iters=300,
+                         max_refine=300)
+    assert got["checks"] == ref["checks"] and got["passes"] == ref["passes"]
+    assert abs(got["iters"] - ref["iters"]) <= 2, (got, ref["iters"])
+    assert abs(got["refine_iters"] - ref["refine_iters"]) <= 3, (got, ref["refine_iters"])
+    assert abs(got["nr_final"] - ref["nr_final"]) <= 2e-4
+    # the full-X and compressed methods run through the same driver
+    s.set_factors(t32(Hi))
+    full = s.solve(method=S.SRC_X, max_iters=300)
+    assert full["iters"] < 300 and full["checks"] == 0
+    s.set_factors(t32(Hi))
+    comp = s.solve(method=S.SRC_COMP, l=l, q_max=8, max_iters=300, max_refine=300)
+    assert comp["nr_final"] <= full["nr_final"] + 1e-2

@@ -7,6 +7,11 @@ from oracle import symnmf as O
 from synth import gaussian_sketch, gmm_points, kernel_matrix_numpy, median_pair_distance, planted_dense, uniform_factor
 
 
+def _gmm(n, seed):
+    pts, labels = gmm_points(n, 8, 5, seed=seed)
+    return kernel_matrix_numpy(pts, median_pair_distance(pts, seed=seed)), labels
+
+
 def _lowrank_sym(n, r, seed):
     rng = np.random.default_rng(seed)
     B = rng.standard_normal((n, r))
@@ -145,3 +150,24 @@ def test_ada_rrf_stops_once_the_residual_stalls():
     _, hs, _ = O.ada_rrf(Xs, rng.standard_normal((300, 12)), 10, tol=1e-3)
     assert all(a - b >= 1e-3 for a, b in zip(hs[:-2], hs[1:-1]))
     assert len(hs) == 10 or hs[-2] - hs[-1] < 1e-3
+
+
+def test_stop_rule_counts_consecutive_small_decreases():
+    # residuals 1.0, 0.5, 0.4999, 0.49985, 0.3, 0.29995, 0.2999, 0.29989, 0.29988, ...: the run of
+    # four small decreases starts after the jump to 0.3 (the one before it is broken)
+    seq = iter([1.0, 0.5, 0.4999, 0.49985, 0.3, 0.29995, 0.2999, 0.29989, 0.29988, 0.2, 0.1])
+    it, nr = O.stop_rule_phase(lambda: next(seq), 100, tol=1e-4, count=4)
+    assert it == 9 and nr == 0.29988
+    seq = iter([1.0, 0.9, 0.8])
+    assert O.stop_rule_phase(lambda: next(seq), 3)[0] == 3  # the cap
+
+
+def test_lai_schedule_reaches_the_full_solution_with_refinement():
+    X, _ = _gmm(600, 3)
+    rng = np.random.default_rng(31)
+    Om = rng.standard_normal((600, 16))
+    H0 = rng.random((600, 5)) * O.init_scale(X, 5)
+    out = O.lai_schedule(X, Om, H0, O.default_alpha(X), q_max=6, max_iters=300, max_refine=300)
+    W, H, _ = O.hals_symnmf(X, H0, O.default_alpha(X), 400, record=False)
+    assert out["iters"] < 300 and out["checks"] >= 2
+    assert out["nr_final"] <= O.normalized_residual(X, W, H) + 5e-3
