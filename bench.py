@@ -469,7 +469,9 @@ def lvs_form(S, dev):
     sv.profile(False)
     out["ms_per_iteration"] = {"lvs_hals": t_lvs / 20 * 1e3, "full_hals": t_full / 20 * 1e3,
                                "speedup": t_full / t_lvs}
-    out["lvs_buckets_ms_per_iteration"] = {"sampling": samp / 10, "mm": mm / 10, "solve": upd / 10}
+    its = max(halves, 1) / 2.0  # two halves per iteration
+    out["lvs_buckets_ms_per_iteration"] = {"sampling": samp / its, "mm": mm / its, "solve": upd / its,
+                                           "halves_profiled": halves}
     # residual after 50 iterations against the oracle's
     sv.init_random(True)
     sv.lvs_iterate(50, tau, sc)

@@ -33,6 +33,26 @@ def init_params(dims, seed):
     return params
 
 
+def round_bf16(a):
+    """Round to bfloat16 (8-bit mantissa), nearest-even on the 16 dropped bits of the float32 value.
+
+    The library's tensor-core products take their operands in this format: the mixed-precision
+    network below rounds exactly those operands, so that its products agree with the GPU's FP32
+    accumulation of the same BF16 values.
+    """
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    keep = (b >> np.uint64(16)) & np.uint64(1)
+    r = ((b + np.uint64(0x7FFF) + keep) >> np.uint64(16)) << np.uint64(16)
+    return (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _q(a, bf16):
+    """An operand of a product: itself, or (float32 then) bfloat16 when `bf16`."""
+    if not bf16:
+        return a
+    return round_bf16(np.asarray(a, dtype=np.float64).astype(np.float32))
+
+
 def softplus(z):
     return np.logaddexp(0.0, z)
 
@@ -41,13 +61,15 @@ def sigmoid(z):
     return 0.5 * (1.0 + np.tanh(0.5 * z))
 
 
-def forward(params, x):
+def forward(params, x, bf16=False):
+    """Network output and the cache of the backward pass.  With `bf16`, the operands of the three
+    products (x, a1, a2 and W1, W2, W3) are rounded to bfloat16; the rest stays FP64."""
     W1, b1, W2, b2, W3, b3 = params
-    z1 = x @ W1 + b1
+    z1 = _q(x, bf16) @ _q(W1, bf16) + b1
     a1 = np.maximum(z1, 0.0)
-    z2 = a1 @ W2 + b2
+    z2 = _q(a1, bf16) @ _q(W2, bf16) + b2
     a2 = np.maximum(z2, 0.0)
-    z3 = a2 @ W3 + b3
+    z3 = _q(a2, bf16) @ _q(W3, bf16) + b3
     return softplus(z3), (x, z1, a1, z2, a2, z3)
 
 
@@ -62,20 +84,23 @@ def gram_loss(Hhat, Hstar):
     return L, dH
 
 
-def backward(params, cache, dout):
-    """Gradients of sum(dout * H0) with respect to all parameters."""
+def backward(params, cache, dout, bf16=False):
+    """Gradients of sum(dout * H0) with respect to all parameters.  With `bf16`, the operands of
+    the five backward products (activations, pre-activation gradients, weights) are rounded to
+    bfloat16, as the library's tensor-core backward pass takes them."""
     W1, b1, W2, b2, W3, b3 = params
     x, z1, a1, z2, a2, z3 = cache
+    q = lambda a: _q(a, bf16)  # noqa: E731
     dz3 = dout * sigmoid(z3)
-    dW3 = a2.T @ dz3
+    dW3 = q(a2).T @ q(dz3)
     db3 = dz3.sum(0)
-    da2 = dz3 @ W3.T
+    da2 = q(dz3) @ q(W3).T
     dz2 = da2 * (z2 > 0)
-    dW2 = a1.T @ dz2
+    dW2 = q(a1).T @ q(dz2)
     db2 = dz2.sum(0)
-    da1 = dz2 @ W2.T
+    da1 = q(dz2) @ q(W2).T
     dz1 = da1 * (z1 > 0)
-    dW1 = x.T @ dz1
+    dW1 = q(x).T @ q(dz1)
     db1 = dz1.sum(0)
     return [dW1, db1, dW2, db2, dW3, db3]
 

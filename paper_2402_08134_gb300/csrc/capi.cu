@@ -173,7 +173,7 @@ static symnmf_status ensure_gemm_ws(symnmf_t h, int N) {
       h->fpack = p;
       h->fpack_bytes = pack;
     }
-    if (!h->colscale) TRY(dalloc(h, &h->colscale, 256));
+    if (!h->colscale) TRY(dalloc(h, &h->colscale, 512));  // one scale per packed column (BN <= 512)
   }
   if (need > h->gemm_ws_floats) {
     if (h->capturing) return fail(h, SYMNMF_ESTATE, "allocation during graph capture");
@@ -1266,15 +1266,14 @@ extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, co
   float* ws = nullptr;
   float* cs = nullptr;
   unsigned* err = nullptr;
-  if ((e = cudaMallocAsync(&pack, (size_t)BN * ldp * es, st)) != cudaSuccess) return to_status(e);
-  if ((e = cudaMallocAsync((void**)&ws, wsf * 4, st)) != cudaSuccess) return to_status(e);
-  if ((e = cudaMallocAsync((void**)&cs, 256 * 4, st)) != cudaSuccess) return to_status(e);
-  if ((e = cudaMallocAsync((void**)&err, 4, st)) != cudaSuccess) return to_status(e);
-  cudaMemsetAsync(err, 0, 4, st);
-  if (fmt == SYMNMF_X_DENSE_BF16)
-    e = pack_ft_bf16(F, n, ldf, N, BN, pack, ldp, st);
-  else
-    e = pack_ft_fp8(F, n, ldf, N, BN, pack, ldp, cs, st);
+  e = cudaMallocAsync(&pack, (size_t)BN * ldp * es, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ws, wsf * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cs, (size_t)BN * 4, st);  // one scale per packed column
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
+  if (e == cudaSuccess)
+    e = fmt == SYMNMF_X_DENSE_BF16 ? pack_ft_bf16(F, n, ldf, N, BN, pack, ldp, st)
+                                   : pack_ft_fp8(F, n, ldf, N, BN, pack, ldp, cs, st);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = standalone_events(&e0, &e1, 2.0 * n * n * N, (double)n * n * es + (double)n * N * (es + 4.0));
   if (e == cudaSuccess)
@@ -1282,10 +1281,8 @@ extern "C" symnmf_status symnmf_dense_xf(int fmt, const void* x, int64_t ldx, co
   unsigned herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFreeAsync(pack, st);
-  cudaFreeAsync(ws, st);
-  cudaFreeAsync(cs, st);
-  cudaFreeAsync(err, st);
+  for (void* p : {pack, (void*)ws, (void*)cs, (void*)err})
+    if (p) cudaFreeAsync(p, st);
   if (e != cudaSuccess) return to_status(e);
   return herr ? SYMNMF_ETIMEOUT : SYMNMF_OK;
 }

@@ -417,12 +417,12 @@ struct TcPlan {
 // products, where F's traffic from L2 would otherwise limit the tensor rate.
 static bool tc_m2(int N) { return N > 128 && N <= 256; }
 
-static TcPlan tc_plan(int64_t n, bool fp8, int bm = TC_BM) {
+static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM) {
   TcPlan p;
   const int kel = fp8 ? 128 : 64;
   p.bm = bm;
-  p.kblocks = (int)((n + kel - 1) / kel);
-  p.mtiles = (int)((n + bm - 1) / bm);
+  p.kblocks = (int)((kdim + kel - 1) / kel);
+  p.mtiles = (int)((m + bm - 1) / bm);
   p.total = (int64_t)p.kblocks * p.mtiles;
   p.G = (int)std::min<int64_t>(num_sms(), p.total);
   p.max_segs = 1;
@@ -434,16 +434,18 @@ static TcPlan tc_plan(int64_t n, bool fp8, int bm = TC_BM) {
   return p;
 }
 
-size_t xf_tc_ws_floats(int64_t n, int BN) {
+size_t tc_gemm_ws_floats(int64_t m, int64_t kdim, int BN) {
   // largest of the plans a product of this width can use
   const int bm = tc_m2(BN) ? 2 * TC_BM : TC_BM;
   size_t need = 0;
   for (int f = 0; f < 2; ++f) {
-    const TcPlan p = tc_plan(n, f != 0, bm);
+    const TcPlan p = tc_plan(m, kdim, f != 0, bm);
     need = std::max(need, (size_t)p.G * p.max_segs * bm * BN);
   }
   return need;
 }
+
+size_t xf_tc_ws_floats(int64_t n, int BN) { return tc_gemm_ws_floats(n, n, BN); }
 
 // Fpack[c, i] = F[i, c] (zero padded to Npad x ldp) through 32 x 32 tiles in
 // shared memory: both the reads of F rows and the writes of Fpack rows coalesce.
@@ -525,6 +527,13 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
                   const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y, int ldy,
                   float* ws, size_t ws_floats, unsigned* err, cudaStream_t st, cudaEvent_t ev_begin,
                   cudaEvent_t ev_end) {
+  return tc_gemm(fmt, X, ldx, n, n, row_scale, Fpack, ldp, col_scale, N, Y, ldy, ws, ws_floats, err, st, ev_begin,
+                 ev_end);
+}
+
+cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, const float* row_scale,
+                    const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y, int ldy, float* ws,
+                    size_t ws_floats, unsigned* err, cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   const bool fp8 = fmt == 3;
   if (!fp8 && fmt != 2) return cudaErrorInvalidValue;
   const int BN = tc_block_n(N);
@@ -534,11 +543,11 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
     return cudaErrorInvalidValue;
   const bool m2 = tc_m2(N);
-  const TcPlan p = tc_plan(n, fp8, m2 ? 2 * TC_BM : TC_BM);
+  const TcPlan p = tc_plan(m, n, fp8, m2 ? 2 * TC_BM : TC_BM);
   if (ws_floats < (size_t)p.G * p.max_segs * p.bm * BN) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   const uint32_t kel = fp8 ? 128 : 64;
-  if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)n, (uint64_t)ldx * es, kel, TC_BM))
+  if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)m, (uint64_t)ldx * es, kel, TC_BM))
     return cudaErrorInvalidValue;
   if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel,
                    (uint32_t)(BN > 256 ? 256 : BN)))
@@ -564,9 +573,9 @@ cudaError_t xf_tc(int fmt, const void* X, int64_t ldx, const float* row_scale, i
   }
   if (ev_end) cudaEventRecord(ev_end, st);
   if (e != cudaSuccess) return e;
-  const int64_t work = n * ((N + 3) / 4);
+  const int64_t work = m * ((N + 3) / 4);
   tc_reduce_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(
-      ws, p.max_segs, BN, p.bm, p.kblocks, p.total, p.G, n, N, Y, ldy, fp8 ? row_scale : nullptr,
+      ws, p.max_segs, BN, p.bm, p.kblocks, p.total, p.G, m, N, Y, ldy, fp8 ? row_scale : nullptr,
       fp8 ? col_scale : nullptr);
   count_launches(1);
   return cudaGetLastError();

@@ -25,7 +25,7 @@ cudaError_t xf_simt(int fmt /*F32 or F64*/, const void* X, int64_t ldx, int64_t 
                     int ldf, int N, float* Y, int ldy, float* ws, size_t ws_floats, cudaStream_t st);
 
 // tcgen05 path: operands are a packed K-major copy of F^T (Npad x ldp).
-int tc_block_n(int N);  // 32, 64, 128 or 256
+int tc_block_n(int N);  // 32, 64, 128, 256 or 512
 size_t xf_tc_ws_floats(int64_t n, int BN);
 cudaError_t pack_ft_bf16(const float* F, int64_t n, int ldf, int N, int Npad, void* out, int64_t ldp,
                          cudaStream_t st);
@@ -35,6 +35,15 @@ cudaError_t xf_tc(int fmt /*BF16 or FP8*/, const void* X, int64_t ldx, const flo
                   int64_t n, const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y,
                   int ldy, float* ws, size_t ws_floats, unsigned* err, cudaStream_t st,
                   cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+
+// Rectangular form: Y (m x N) = A (m x kdim, row-major, ld lda, BF16 or E4M3
+// with row scales) times F, F^T packed as for xf_tc (N x ldp, ldp >= kdim).
+// Rows of A past m and columns past kdim read as zero (TMA fill).
+size_t tc_gemm_ws_floats(int64_t m, int64_t kdim, int BN);
+cudaError_t tc_gemm(int fmt, const void* A, int64_t lda, int64_t m, int64_t kdim, const float* row_scale,
+                    const void* Fpack, int64_t ldp, const float* col_scale, int N, float* Y, int ldy, float* ws,
+                    size_t ws_floats, unsigned* err, cudaStream_t st, cudaEvent_t ev_begin = nullptr,
+                    cudaEvent_t ev_end = nullptr);
 
 // ------------------------------------------------------------------ sparse
 cudaError_t csr_xf(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,

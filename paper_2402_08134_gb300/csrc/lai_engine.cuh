@@ -272,9 +272,14 @@ __device__ __forceinline__ void le_finish(const LaiArgs& a, const LeTiles& tl, c
 // F^T F), the FP32 state of the next half to state[side], and after the H half
 // of sweep t >= 0 this CTA's objective share to objp[t].
 constexpr int LE_BATCH = 8;
+constexpr int LE_STASH = 512;  // slice positions whose W-half sums stay in shared memory
 
-__device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int t, float* red, double* shd) {
-  (void)red;
+// stash: this CTA's W-half sums of its slice (positions c0 + i), written by the
+// side-0 reduction and read by the side-1 one (same slicing), when the slice
+// fits LE_STASH; lam_s: lambda in shared memory.  Both keep the H half's
+// objective terms off dependent global loads.
+__device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int t, double* shd, double* stash,
+                                                const double* lam_s) {
   const int k = a.k, l = a.l, k4 = (k + 3) & ~3, gp = a.gp;
   const int E = le_entries(l, k), EP = le_rec_entries(l, k), SL = le_state_floats(l, k, gp);
   const int lk = l * k, kt = k4 / 4, tm = (((l + 3) & ~3) / 4) * kt;
@@ -285,6 +290,7 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
   // tr and dd (the last column, EP a multiple of 4) never straddle two CTAs
   const int per = ((EP + gridDim.x - 1) / gridDim.x + 3) & ~3;
   const int c0 = blockIdx.x * per, c1 = min(EP, c0 + per);
+  const bool stashed = per <= LE_STASH;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double share = 0.0;
   for (int col = c0 + 4 * wid; col < c1; col += 4 * (LE_THREADS / 32)) {
@@ -325,17 +331,22 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
     for (int e = 0; e < 4; ++e) {
       const int idx = col + e;
       const double v = (double)hi[e] + (double)lo[e];
+      double v_w = 0.0;  // the W half's sum at this position (side 1)
+      if (stashed) {
+        if (side == 0) stash[idx - c0] = v;
+        else v_w = stash[idx - c0];
+      }
       const int tile = idx >> 4, p = (idx >> 2) & 3, q = idx & 3;
       if (tile < tm) {
         const int i = 4 * (tile / kt) + p, j = 4 * (tile % kt) + q;
         if (i < l && j < k) {
           fin[i * k + j] = v;
-          st[i * k4 + j] = (float)(a.lam[i] * v);
+          st[i * k4 + j] = (float)(lam_s[i] * v);
           // the H half's rows used M~ = fl32(lambda U^T W), rounded once and shared by
           // every row, so tr(H^T U M~) misses the exact tr by sum (U^T H) .* (M~ - M):
-          // added back here, where U^T H (this sum, v) and U^T W (fin[0]) are in FP64
+          // added back here, where U^T H (this sum, v) and U^T W are in FP64
           if (side == 1 && t >= 0) {
-            const double m = a.lam[i] * __ldcg(a.fin + i * k + j);
+            const double m = lam_s[i] * (stashed ? v_w : __ldcg(a.fin + i * k + j));
             share += 2.0 * v * ((double)(float)m - m);
           }
         }
@@ -350,7 +361,8 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
           st[l * k4 + j * gp + i] = (float)v;
           if (i == j) st[l * k4 + gp * gp + i] = 1.0f / ((float)v + a.alpha);
           // (W^T W)_ij (H^T H)_ij over all (i, j): an off-diagonal tile holds each pair once
-          if (side == 1 && t >= 0) share += (bi == bj ? 1.0 : 2.0) * __ldcg(a.fin + lk + i * k + j) * v;
+          if (side == 1 && t >= 0)
+            share += (bi == bj ? 1.0 : 2.0) * (stashed ? v_w : __ldcg(a.fin + lk + i * k + j)) * v;
         }
       }
     }
@@ -408,6 +420,9 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
   float* red = Yt + k4 * P;    // 16 x LE_THREADS
   auto col = [P](int c) { return c * P + ((c >> 2) & 7) * 4; };  // start of column c
   __shared__ double shd[32];
+  __shared__ double stash[LE_STASH];
+  __shared__ double lam_s[96];
+  for (int i = threadIdx.x; i < a.l; i += LE_THREADS) lam_s[i] = a.lam[i];
 
   const int tid = threadIdx.x;
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
     le_settle(acc, cmp);
     le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
     if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-    le_reduce_slice(a, 1, -1, red, shd);
+    le_reduce_slice(a, 1, -1, shd, stash, lam_s);
     if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
   }
   le_load_state(a, 1, Ms);
@@ -538,7 +553,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
       le_settle(acc, cmp);
       le_finish(a, tl, acc, red, trv, ddv);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-      le_reduce_slice(a, side, t, red, shd);
+      le_reduce_slice(a, side, t, shd, stash, lam_s);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
       le_load_state(a, side, Ms);
     }
@@ -579,6 +594,9 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
   float* Fu = Fx + TR * fs;              // TR x fs: rows being updated
   float* red = Fu + TR * fs;             // 16 x LE_THREADS: row-group combine
   __shared__ double shd[32];
+  __shared__ double stash[LE_STASH];
+  __shared__ double lam_s[96];
+  for (int i = threadIdx.x; i < a.l; i += LE_THREADS) lam_s[i] = a.lam[i];
 
   const int tid = threadIdx.x;
   const int64_t r0 = (a.n * blockIdx.x) / gridDim.x;
@@ -663,7 +681,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
     le_settle(acc, cmp);
     le_finish(a, tl, acc, red, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
     if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-    le_reduce_slice(a, 1, -1, red, shd);
+    le_reduce_slice(a, 1, -1, shd, stash, lam_s);
     if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
   }
   le_load_state(a, 1, Ms);
@@ -719,7 +737,7 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
       le_settle(acc, cmp);
       le_finish(a, tl, acc, red, trv, ddv);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
-      le_reduce_slice(a, side, t, red, shd);
+      le_reduce_slice(a, side, t, shd, stash, lam_s);
       if (!grid_sync_bounded(a.bar, a.err, epoch)) return;
       le_load_state(a, side, Ms);
     }
@@ -747,7 +765,7 @@ inline size_t smem_optin_limit() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-  return v > 1024 ? (size_t)(v - 1024) : 0;  // room for the kernels' static shared memory
+  return v > 8192 ? (size_t)(v - 8192) : 0;  // room for the kernels' static shared memory (~5.2 KB)
 }
 
 template <int KMAX>

@@ -13,6 +13,15 @@ from ._gpu_util import np64, product_bound, t32, t64
 pytestmark = pytest.mark.gpu
 
 
+def _fp8_col_scale(Ft):
+    """Column scales of the E4M3 packing: max |F[:, c]| / 448 by IEEE division in float32 (1 for a
+    zero column).  torch's division by a Python scalar multiplies by a rounded reciprocal instead,
+    which can move a scale by one ulp and, through it, flip an E4M3 rounding of that column."""
+    mx = Ft.abs().amax(dim=0).cpu().numpy().astype(np.float32)
+    cs = np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    return torch.tensor(cs, device=Ft.device)
+
+
 def _sym(n, seed):
     rng = np.random.default_rng(seed)
     A = rng.random((n, n))
@@ -82,7 +91,7 @@ def test_tcgen05_product_is_unbiased_over_long_k(S, fmt, N):
         x8, rs = S.quantize_fp8(Xt)
         Y = S.dense_xf(x8, Ft, row_scale=rs, gemm=S.GEMM_TC)
         Xe = x8[:, :n].view(torch.float8_e4m3fn).double() * rs.double()[:, None]
-        cs = Ft.abs().amax(dim=0) / 448.0
+        cs = _fp8_col_scale(Ft)
         Fq = (Ft / cs).to(torch.float8_e4m3fn).double() * cs.double()
         ref = Xe @ Fq
     rel = ((Y.double() - ref) / ref).cpu().numpy()
@@ -102,8 +111,7 @@ def test_tcgen05_fp8_product(S, n, N):
     # reference: the same E4M3 codes, dequantised, times the E4M3-quantised F
     Xq = x8[:, :n].view(torch.float8_e4m3fn).double() * rs.double()[:, None]
     Ft = t32(F)
-    cs = (Ft.abs().amax(dim=0) / 448.0)
-    cs = torch.where(cs > 0, cs, torch.ones_like(cs))
+    cs = _fp8_col_scale(Ft)
     Fq = (Ft / cs).to(torch.float8_e4m3fn).double() * cs.double()
     ref = (Xq @ Fq).cpu().numpy()
     bound = product_bound(Xq.cpu().numpy(), Fq.cpu().numpy(), 2e-6)

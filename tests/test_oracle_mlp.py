@@ -1,8 +1,10 @@
 """Pins for the oracle's warm-start network: finite differences, loss identity, Adam closed form."""
 
 import numpy as np
+import pytest
 
 from oracle import mlp
+from oracle import mlp as OM
 
 
 def _net(seed=0):
@@ -63,3 +65,30 @@ def test_forward_nonnegative_output():
     x = np.random.default_rng(2).standard_normal((10, 6))
     out, _ = mlp.forward(_net(3), x)
     assert (out > 0).all()
+
+
+def test_bf16_rounding_matches_torch_and_is_nearest_even():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-6, 6, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, -2.5e-30]])
+    got = OM.round_bf16(a)
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    np.testing.assert_array_equal(got, ref)
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and goes to the even mantissa (1);
+    # 1 + 3 * 2^-8 goes up to 1 + 2^-6
+    assert OM.round_bf16(np.array([1.00390625]))[0] == 1.0
+    assert OM.round_bf16(np.array([1.01171875]))[0] == 1.015625
+
+
+def test_bf16_network_reduces_to_fp64_network_on_representable_values():
+    # with x and every weight already bfloat16 values, the mixed-precision forward differs from the
+    # FP64 one only through the rounding of the hidden activations
+    rng = np.random.default_rng(12)
+    dims = (8, 16, 16, 4)
+    params = [OM.round_bf16(p) for p in OM.init_params(dims, 3)]
+    x = OM.round_bf16(rng.standard_normal((20, 8)))
+    y64, _ = OM.forward(params, x)
+    y16, _ = OM.forward(params, x, bf16=True)
+    assert np.abs(y16 - y64).max() < 2e-2 * np.abs(y64).max()
+    assert not np.array_equal(y16, y64)
