@@ -317,9 +317,13 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         df_add(hi[e], lo[e], __shfl_xor_sync(0xffffffffu, hi[e], o), __shfl_xor_sync(0xffffffffu, lo[e], o));
-    if (lane != 0) continue;
+    // every lane holds the column's sums after the xor tree: lanes 0..3 map one
+    // position each (FP64 is a narrow pipe on this part: four short chains in
+    // parallel instead of one long one)
+    if (lane >= 4) continue;
     if (col == EP - 4) {
       // tr and dd: hi/lo pairs of double-float sums
+      if (lane != 0) continue;
       const double tr = (double)hi[0] + (double)lo[0] + (double)hi[1] + (double)lo[1];
       const double dd = (double)hi[2] + (double)lo[2] + (double)hi[3] + (double)lo[3];
       fin[lk + k * k] = tr;
@@ -327,10 +331,12 @@ __device__ __forceinline__ void le_reduce_slice(const LaiArgs& a, int side, int 
       if (side == 1 && t >= 0) share += -2.0 * tr + a.alpha_d * dd;
       continue;
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    {
+      const int e = lane;
+      const float he = e == 0 ? hi[0] : e == 1 ? hi[1] : e == 2 ? hi[2] : hi[3];
+      const float le = e == 0 ? lo[0] : e == 1 ? lo[1] : e == 2 ? lo[2] : lo[3];
       const int idx = col + e;
-      const double v = (double)hi[e] + (double)lo[e];
+      const double v = (double)he + (double)le;
       double v_w = 0.0;  // the W half's sum at this position (side 1)
       if (stashed) {
         if (side == 0) stash[idx - c0] = v;

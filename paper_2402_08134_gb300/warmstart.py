@@ -23,17 +23,59 @@ from . import MLP, SRC_LAI, SRC_X, Solver, gaussian
 OMEGA_SEED = 0x5EED0F0E6A
 
 
-def make_instance(n, d, c, seed, device):
-    """Kernel matrix of one seeded instance on the device: (X float32, X bfloat16 padded to 8 columns)."""
-    from synth import gmm_points, kernel_matrix_torch, median_pair_distance
+def instance_points(n, d, c, seed):
+    """The seeded points of one instance and its kernel width (host side, numpy)."""
+    from synth import gmm_points, median_pair_distance
 
     pts, labels = gmm_points(n, d, c, seed=seed, weights="dirichlet")
-    sigma = median_pair_distance(pts, seed=seed)
-    Xf = kernel_matrix_torch(pts, sigma, device)
+    return pts, median_pair_distance(pts, seed=seed), labels
+
+
+def instance_matrix(pts, sigma, device, math_dtype=None):
+    """(X float32, X bfloat16 padded to 8 columns) of one instance on the device."""
+    from synth import kernel_matrix_torch
+
+    n = pts.shape[0]
+    Xf = kernel_matrix_torch(pts, sigma, device, math_dtype=math_dtype)
     ld = (n + 7) // 8 * 8
     Xb = torch.zeros((n, ld), dtype=torch.bfloat16, device=device)
     Xb[:, :n] = Xf.to(torch.bfloat16)
+    return Xf, Xb
+
+
+def make_instance(n, d, c, seed, device, math_dtype=None):
+    """Kernel matrix of one seeded instance on the device: (X float32, X bfloat16 padded to 8 columns).
+
+    Distances are formed in `math_dtype` (default float64, as the oracle forms them; float32 is
+    enough for training instances and much faster on this part's FP64 units)."""
+    pts, sigma, labels = instance_points(n, d, c, seed)
+    Xf, Xb = instance_matrix(pts, sigma, device, math_dtype)
     return Xf, Xb, labels
+
+
+def training_set(n, d, c, k, l, q, sweeps, seeds, omega, device, math_dtype=None, workers=8):
+    """(features, H*) of every seed: the instance solved by the library (sketch with the shared
+    Omega, LAI sweeps, 2 full-X sweeps).  The host draws the next instances' points on a thread
+    pool while the device solves the current one."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    data = []
+    seeds = list(seeds)
+    window = 2 * workers  # instances drawn ahead (bounded host memory)
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        futs = [pool.submit(instance_points, n, d, c, s) for s in seeds[:window]]
+        for i, s in enumerate(seeds):
+            if i + window < len(seeds):
+                futs.append(pool.submit(instance_points, n, d, c, seeds[i + window]))
+            pts, sigma, _ = futs[i].result()
+            futs[i] = None
+            Xf, Xb = instance_matrix(pts, sigma, device, math_dtype)
+            sv, feats, _ = solve(Xb, Xf, k, l, q, sweeps, seed=s, omega=omega)
+            H, _ = sv.factors()
+            data.append((feats.clone(), H.clone()))
+            sv.close()
+            del Xf, Xb
+    return data
 
 
 def solve(Xb, Xf, k, l, q, sweeps, refine=2, seed=1, net=None, omega=None, record=False):

@@ -96,8 +96,13 @@ def median_pair_distance(points: np.ndarray, seed: int, npairs: int = 1_000_000)
     return float(np.median(dist))
 
 
-def kernel_matrix_numpy(points: np.ndarray, sigma: float, dtype=np.float64) -> np.ndarray:
-    """X_ij = exp(-||x_i - x_j||^2 / sigma^2) with an exact unit diagonal (float64 math)."""
+def kernel_matrix_numpy(points: np.ndarray, sigma: float, dtype=np.float64, block: int | None = None) -> np.ndarray:
+    """X_ij = exp(-||x_i - x_j||^2 / sigma^2) with an exact unit diagonal (float64 math).
+
+    With `block`, the matrix is built block by block (upper block triangle, mirrored), so that
+    the peak memory is the result plus one block instead of several n x n temporaries."""
+    if block is not None:
+        return _kernel_matrix_blocked(points, sigma, dtype, block)
     sq = (points ** 2).sum(axis=1)
     d2 = sq[:, None] + sq[None, :] - 2.0 * (points @ points.T)
     np.maximum(d2, 0.0, out=d2)
@@ -107,17 +112,40 @@ def kernel_matrix_numpy(points: np.ndarray, sigma: float, dtype=np.float64) -> n
     return X.astype(dtype, copy=False)
 
 
-def kernel_matrix_torch(points, sigma: float, device, dtype=None, block: int = 4096):
-    """Same kernel matrix built on a torch device in float32 math, row block by row block.
+def _kernel_matrix_blocked(points, sigma, dtype, block):
+    n = points.shape[0]
+    sq = (points ** 2).sum(axis=1)
+    X = np.empty((n, n), dtype=dtype)
+    inv = 1.0 / (sigma * sigma)
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        for c0 in range(r0, n, block):
+            c1 = min(n, c0 + block)
+            d2 = sq[r0:r1, None] + sq[None, c0:c1] - 2.0 * (points[r0:r1] @ points[c0:c1].T)
+            np.maximum(d2, 0.0, out=d2)
+            if r0 == c0:
+                np.fill_diagonal(d2, 0.0)
+            blk = np.exp(-d2 * inv)
+            if r0 == c0:
+                blk = 0.5 * (blk + blk.T)
+            X[r0:r1, c0:c1] = blk
+            if c0 != r0:
+                X[c0:c1, r0:r1] = blk.T
+    return X
 
-    `points` is a numpy array; the result has `dtype` (default float32).  The
-    matrix is symmetrised exactly by building only the upper block triangle
-    and mirroring it.
+
+def kernel_matrix_torch(points, sigma: float, device, dtype=None, block: int = 4096, math_dtype=None):
+    """Same kernel matrix built on a torch device, row block by row block.
+
+    `points` is a numpy array; the result has `dtype` (default float32) and the
+    distances are formed in `math_dtype` (default float64).  The matrix is
+    symmetrised exactly by building only the upper block triangle and
+    mirroring it.
     """
     import torch
 
     dtype = dtype or torch.float32
-    P = torch.as_tensor(points, dtype=torch.float64, device=device)
+    P = torch.as_tensor(points, dtype=math_dtype or torch.float64, device=device)
     n = P.shape[0]
     sq = (P * P).sum(dim=1)
     X = torch.empty((n, n), dtype=dtype, device=device)
