@@ -81,7 +81,7 @@ class _FakeSolver:
     def init_random(self, scaled):
         self.log.append(("init", scaled))
 
-    def lai_sketch(self, l, q):
+    def lai_sketch(self, l, q, omega=None):
         self.log.append(("sketch", l, q))
 
     def sweep(self, m, source, record):
