@@ -455,8 +455,19 @@ def batched_form(S, dev, sweeps=100):
     gold = golden("c4_reference.json")
     if gold is not None:
         ref = np.asarray(gold["nr"])
-        out["nr_max_abs_diff_vs_oracle"] = float(np.max(np.abs(np.asarray(nr_b) - ref)))
-        out["nr_within_1e-3_of_oracle"] = bool(np.all(np.abs(np.asarray(nr_b) - ref) <= 1e-3))
+        db = np.abs(np.asarray(nr_b) - ref)
+        dp = np.abs(np.asarray(nr_p) - ref)
+        out["nr_max_abs_diff_vs_oracle"] = float(db.max())
+        out["nr_within_1e-3_of_oracle"] = bool(np.all(db <= 1e-3))
+        out["nr_vs_oracle"] = {
+            "batched_bf16": {"within_1e-3": int((db <= 1e-3).sum()), "median_abs_diff": float(np.median(db)),
+                             "max_abs_diff": float(db.max())},
+            "plain_fp32": {"within_1e-3": int((dp <= 1e-3).sum()), "median_abs_diff": float(np.median(dp)),
+                           "max_abs_diff": float(dp.max())},
+            "worst_batched": [{"problem": int(i // 4), "restart": int(i % 4), "n": specs[i // 4]["n"],
+                               "k": specs[i // 4]["k"], "nr": float(nr_b[i]), "oracle": float(ref[i]),
+                               "plain_fp32": float(nr_p[i])} for i in np.argsort(-db)[:4]],
+        }
     return out
 
 

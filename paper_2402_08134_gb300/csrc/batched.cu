@@ -17,6 +17,7 @@
 
 #include "../../include/symnmf.h"
 #include "common.cuh"
+#include "hals_row.cuh"
 #include "handle.h"
 #include "kernels.h"
 #include "tc_common.cuh"
@@ -40,6 +41,7 @@ struct HalsProb {
   long long row_off;   // first global row
   long long tile_off;  // first 64-row tile (HALS) / 256-row chunk (Gram) handled below
   long long chunk_off;
+  long long gp_off;    // padded FP32 Grams and inverses: R (KM^2 + KM), KM = k padded to 8/16/24/32
   int n, k, R, pr_off;  // pr_off: first (problem, restart) slot
   double alpha;
 };
@@ -251,182 +253,287 @@ __device__ __forceinline__ int find_le(const long long* off, int count, long lon
   return lo;
 }
 
-__global__ void grouped_reduce_kernel(ReduceTab tab, int nprob, const float* __restrict__ partials,
-                                      int max_segs, long long total, int G, long long total_rows,
-                                      float* Y_all) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total_rows * GB_BN) return;
-  const long long gr = t / GB_BN;
-  const int c = (int)(t - gr * GB_BN);
-  const int p = find_le(tab.row_off, nprob, gr);
-  const int w = tab.width[p];
-  if (c >= w) return;
-  const long long r = gr - tab.row_off[p];
-  const long long tile = r / TC_BM;
-  const int kb = tab.kblocks[p];
+// One block per global 128-row tile: the CTAs whose k ranges covered the tile
+// (and the segment each stored it in) are found once, then the block sums
+// their partial tiles in CTA order (deterministic) with float4 loads and
+// writes the tile's rows of Y.
+constexpr int GR_TABLE = 512;  // covering CTAs held in shared memory
+
+__global__ void __launch_bounds__(256) grouped_reduce_kernel(ReduceTab tab, int nprob,
+                                                             const float* __restrict__ partials, int max_segs,
+                                                             long long total, int G, float* Y_all) {
+  __shared__ int qs[GR_TABLE], segs[GR_TABLE];
+  const long long gt = blockIdx.x;  // global tile
+  const int p = find_le(tab.tile_off, nprob, gt);
+  const long long tile = gt - tab.tile_off[p];
+  const int kb = tab.kblocks[p], w = tab.width[p];
   const long long f_it = tab.it_off[p] + tile * kb, l_it = f_it + kb - 1;
-  const long long gt = tab.tile_off[p] + tile;
   const long long c0 = ((f_it + 1) * G - 1) / total, c1 = ((l_it + 1) * G - 1) / total;
-  float s = 0.f;
-  for (long long q = c0; q <= c1; ++q) {
+  const int nq = (int)(c1 - c0 + 1);
+  auto seg_of = [&](long long q) {
     const long long itb = (q * total) / G;
     const int pb = find_le(tab.it_off, nprob, itb);
-    const long long gtb = tab.tile_off[pb] + (itb - tab.it_off[pb]) / tab.kblocks[pb];
-    const long long seg = gt - gtb;
-    s += partials[((q * max_segs + seg) * TC_BM + (r - tile * TC_BM)) * GB_BN + c];
+    return (int)(gt - (tab.tile_off[pb] + (itb - tab.it_off[pb]) / tab.kblocks[pb]));
+  };
+  for (int e = threadIdx.x; e < nq && e < GR_TABLE; e += blockDim.x) {
+    qs[e] = (int)(c0 + e);
+    segs[e] = seg_of(c0 + e);
   }
-  Y_all[tab.f_off[p] + r * w + c] = s;
+  __syncthreads();
+  const long long r0 = tab.row_off[p] + tile * TC_BM;
+  const int rows = (int)min((long long)TC_BM, tab.row_off[p + 1] - r0);
+  float* Y = Y_all + tab.f_off[p] + tile * TC_BM * w;
+  const bool vec = (w % 4) == 0 && (tab.f_off[p] % 4) == 0;
+  const int w4 = (w + 3) / 4;
+  for (int e = threadIdx.x; e < rows * w4; e += blockDim.x) {
+    const int rr = e / w4, c = 4 * (e - rr * w4);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < nq; ++i) {
+      const long long q = i < GR_TABLE ? qs[i] : c0 + i;
+      const int seg = i < GR_TABLE ? segs[i] : seg_of(c0 + i);
+      const float4 v =
+          __ldcs(reinterpret_cast<const float4*>(partials + ((q * max_segs + seg) * TC_BM + rr) * GB_BN + c));
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    float* yr = Y + (long long)rr * w + c;
+    if (vec) {
+      *reinterpret_cast<float4*>(yr) = acc;
+    } else {
+      const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+      for (int u = 0; u < 4 && c + u < w; ++u) yr[u] = a4[u];
+    }
+  }
 }
 
-// F^T of every problem packed as BF16, bn_p rows of ldp_p (zero padded).
-__global__ void grouped_pack_kernel(const HalsProb* hp, const long long* pack_off, const int* bn,
-                                    const long long* ldp, int nprob, long long total, const float* F_all,
-                                    __nv_bfloat16* out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int p = find_le(pack_off, nprob, t);
-  const long long e = t - pack_off[p];
-  const long long L = ldp[p];
-  const long long c = e / L, i = e - c * L;
-  const HalsProb& P = hp[p];
+// F^T of every problem packed as BF16, bn_p rows of ldp_p (zero padded): one
+// block per 64-row tile (the HALS tiles), staged through shared memory so that
+// both the reads of F rows and the writes of packed rows coalesce.
+constexpr int GP_ROWS = 64, GP_PITCH = 128 + 1;
+
+__global__ void __launch_bounds__(256) grouped_pack_kernel(const HalsProb* __restrict__ hp,
+                                                           const long long* tile_off, int nprob,
+                                                           const long long* pack_off, const int* bn,
+                                                           const long long* ldp, const float* F_all,
+                                                           __nv_bfloat16* out) {
+  __shared__ float Fs[GP_ROWS * GP_PITCH];
+  const int p = find_le(tile_off, nprob, (long long)blockIdx.x);
+  const HalsProb P = hp[p];
   const int w = P.R * P.k;
-  const float v = (c < w && i < P.n) ? F_all[P.f_off + i * w + c] : 0.f;
-  out[t] = __float2bfloat16_rn(v);
+  const long long base = (blockIdx.x - tile_off[p]) * GP_ROWS;
+  const int rows = (int)min((long long)GP_ROWS, (long long)P.n - base);
+  const float* F = F_all + P.f_off + base * w;
+  for (int e = threadIdx.x; e < GP_ROWS * w; e += blockDim.x) {
+    const int rr = e / w, c = e - rr * w;
+    Fs[rr * GP_PITCH + c] = rr < rows ? F[e] : 0.f;
+  }
+  __syncthreads();
+  const long long L = ldp[p];
+  const int bnp = bn[p];
+  __nv_bfloat16* o = out + pack_off[p];
+  for (int e = threadIdx.x; e < bnp * GP_ROWS; e += blockDim.x) {
+    const int c = e / GP_ROWS, rr = e - c * GP_ROWS;
+    const long long i = base + rr;
+    if (i < L) o[c * L + i] = __float2bfloat16_rn(c < w ? Fs[rr * GP_PITCH + c] : 0.f);
+  }
 }
 
 // ----------------------------------------------------------- grouped HALS
 
 constexpr int GH_ROWS = 64;
 
+// (hi, lo) += (h2, l2), double-float (Dekker's two-sum)
+__device__ __forceinline__ void gb_df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2;
+  const float bb = s - hi;
+  lo += ((hi - (s - bb)) + (h2 - bb)) + l2;
+  hi = s;
+}
+
+// The row work of one thread for a problem of width k <= KMAX (G rows padded to KMAX).
 template <int KMAX>
-__global__ void __launch_bounds__(GH_ROWS) grouped_hals_kernel(const HalsProb* __restrict__ hp,
-                                                               const long long* tile_off, int nprob,
-                                                               float* Fu_all, const float* Ff_all,
-                                                               const float* Y_all, const double* Gd_all,
-                                                               double* part, unsigned* err) {
-  extern __shared__ __align__(16) float sm[];
-  const int p = find_le(tile_off, nprob, (long long)blockIdx.x);
-  const HalsProb P = hp[p];
-  const int k = P.k, R = P.R, RW = R * k, Pd = RW + 1;
-  const long long tile = blockIdx.x - tile_off[p];
-  float* Gs = sm;
-  float* inv = Gs + R * k * k;
-  float* Ys = inv + R * k;
-  float* Hs = Ys + GH_ROWS * Pd;
-  float* Ws = Hs + GH_ROWS * Pd;
-  const float alpha = (float)P.alpha;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < R * k * k; e += GH_ROWS) Gs[e] = (float)Gd_all[P.g_off + e];
-  __syncthreads();
-  for (int e = tid; e < R * k; e += GH_ROWS) {
-    const int g = e / k, i = e - g * k;
-    inv[e] = 1.0f / (Gs[g * k * k + i * k + i] + alpha);
-  }
-  const long long base = tile * GH_ROWS;
-  const int rows = (int)min((long long)GH_ROWS, (long long)P.n - base);
-  const float* Ff = Ff_all + P.f_off;
-  float* Fu = Fu_all + P.f_off;
-  const float* Y = Y_all + P.f_off;
-  for (int e = tid; e < rows * RW; e += GH_ROWS) {
-    const int rr = e / RW, c = e - rr * RW;
-    Hs[rr * Pd + c] = Ff[(base + rr) * RW + c];
-    Ws[rr * Pd + c] = Fu[(base + rr) * RW + c];
-    Ys[rr * Pd + c] = Y[(base + rr) * RW + c];
-  }
-  __syncthreads();
-  double tr[GB_MAXR], dd[GB_MAXR];
+__device__ __forceinline__ void grouped_hals_row(const HalsProb& P, int g, long long row, float* Fu_all,
+                                                 const float* Ff_all, const float* Y_all, const float* Gs,
+                                                 const float* inv, float alpha, unsigned* err, float2& trv,
+                                                 float2& ddv) {
+  const int k = P.k, RW = P.R * k;
+  const long long o = P.f_off + row * RW + (long long)g * k;
+  // z = Y + alpha F_fix (as the row routine forms it), so that only w and z
+  // stay in registers; Y and F_fix are read again (cache hits) for the sums
+  float w[KMAX], z[KMAX];
+  if ((k & 3) == 0 && (o & 3) == 0) {  // 16-byte row segments
 #pragma unroll
-  for (int g = 0; g < GB_MAXR; ++g) tr[g] = dd[g] = 0.0;
+    for (int q = 0; q < KMAX / 4; ++q) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), h = a, y = a;
+      if (4 * q < k) {
+        a = *reinterpret_cast<const float4*>(Fu_all + o + 4 * q);
+        h = *reinterpret_cast<const float4*>(Ff_all + o + 4 * q);
+        y = *reinterpret_cast<const float4*>(Y_all + o + 4 * q);
+      }
+      w[4 * q] = a.x, w[4 * q + 1] = a.y, w[4 * q + 2] = a.z, w[4 * q + 3] = a.w;
+      z[4 * q] = fmaf(alpha, h.x, y.x), z[4 * q + 1] = fmaf(alpha, h.y, y.y);
+      z[4 * q + 2] = fmaf(alpha, h.z, y.z), z[4 * q + 3] = fmaf(alpha, h.w, y.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      w[j] = j < k ? Fu_all[o + j] : 0.f;
+      z[j] = j < k ? fmaf(alpha, Ff_all[o + j], Y_all[o + j]) : 0.f;
+    }
+  }
+  hals_row_columns<KMAX>(w, z, 0.f, k, reinterpret_cast<const float4*>(Gs + g * KMAX * KMAX), inv + g * KMAX,
+                         [](int) { return 0.f; }, [](int, float) {});
   bool bad = false;
-  if (tid < rows) {
-    float* yr = Ys + tid * Pd;
-    const float* hr = Hs + tid * Pd;
-    float* wr = Ws + tid * Pd;
-#pragma unroll 1
-    for (int g = 0; g < R; ++g) {
-      const float* Gg = Gs + g * k * k;
-      const int o = g * k;
-      float w[KMAX];
+  float t0 = 0.f, t1 = 0.f, d0 = 0.f, d1 = 0.f;
 #pragma unroll
-      for (int j = 0; j < KMAX; ++j) w[j] = j < k ? wr[o + j] : 0.f;
-#pragma unroll
-      for (int i = 0; i < KMAX; ++i) {
-        if (i < k) {
-          float acc = fmaf(alpha, hr[o + i], yr[o + i]);
-#pragma unroll
-          for (int j = 0; j < KMAX; ++j)
-            if (j != i && j < k) acc = fmaf(-w[j], Gg[j * k + i], acc);
-          w[i] = fmaxf(acc * inv[o + i], 0.f);
-        }
+  for (int j = 0; j < KMAX; ++j)
+    if (j < k) {
+      if (!isfinite(w[j])) bad = true;
+      Fu_all[o + j] = w[j];
+      const float yj = Y_all[o + j];
+      const float d = w[j] - Ff_all[o + j];
+      if (j & 1) {
+        t1 = fmaf(w[j], yj, t1);
+        d1 = fmaf(d, d, d1);
+      } else {
+        t0 = fmaf(w[j], yj, t0);
+        d0 = fmaf(d, d, d0);
       }
-      double t0 = 0.0, d0 = 0.0;
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < k) {
-          if (!isfinite(w[j])) bad = true;
-          wr[o + j] = w[j];
-          t0 += (double)w[j] * (double)yr[o + j];
-          const float d = w[j] - hr[o + j];
-          d0 += (double)d * (double)d;
-        }
-#pragma unroll
-      for (int q = 0; q < GB_MAXR; ++q)
-        if (q == g) {
-          tr[q] = t0;
-          dd[q] = d0;
-        }
     }
-  }
-  __syncthreads();
-  for (int e = tid; e < rows * RW; e += GH_ROWS) {
-    const int rr = e / RW, c = e - rr * RW;
-    Fu[(base + rr) * RW + c] = Ws[rr * Pd + c];
-  }
   if (bad) set_error(err, ERR_NAN);
-  __shared__ double sh[32];
-#pragma unroll 1
-  for (int g = 0; g < R; ++g) {
-    double a = 0.0, b = 0.0;
-#pragma unroll
-    for (int q = 0; q < GB_MAXR; ++q)
-      if (q == g) {
-        a = tr[q];
-        b = dd[q];
-      }
-    a = block_sum(a, sh);
-    b = block_sum(b, sh);
-    if (tid == 0) {
-      atomicAdd(part + 2 * (P.pr_off + g), a);
-      atomicAdd(part + 2 * (P.pr_off + g) + 1, b);
+  trv.x = t0 + t1;
+  ddv.x = d0 + d1;
+}
+
+// The fixed factor's Grams as the HALS blocks read them: per problem R zero-padded
+// KM x KM FP32 matrices with the diagonal zeroed, then R x KM values
+// 1 / (G_ii + alpha) (0 past k).  One block per problem.
+__device__ __forceinline__ int gh_km(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 24 ? 24 : 32; }
+
+__global__ void __launch_bounds__(256) grouped_gram_prep_kernel(const HalsProb* __restrict__ hp,
+                                                                const double* __restrict__ Gd_all, float* Gp_all) {
+  const HalsProb P = hp[blockIdx.x];
+  const int k = P.k, R = P.R, KM = gh_km(k);
+  float* Gp = Gp_all + P.gp_off;
+  for (int e = threadIdx.x; e < R * (KM * KM + KM); e += blockDim.x) {
+    float v;
+    if (e < R * KM * KM) {
+      const int g = e / (KM * KM), rem = e - g * KM * KM;
+      const int i = rem / KM, j = rem - i * KM;
+      v = (i < k && j < k && i != j) ? (float)Gd_all[P.g_off + (long long)g * k * k + i * k + j] : 0.f;
+    } else {
+      const int e2 = e - R * KM * KM, g = e2 / KM, i = e2 - g * KM;
+      v = i < k ? 1.0f / ((float)Gd_all[P.g_off + (long long)g * k * k + i * k + i] + (float)P.alpha) : 0.f;
     }
+    Gp[e] = v;
   }
 }
 
-// Per-restart Grams of every problem: blocks own 256-row chunks; FP32 over
-// 32-row sub-chunks, FP64 per thread, one FP64 atomic per entry per block.
-constexpr int GG_CHUNK = 256, GG_SUB = 32, GG_THREADS = 256;
+// One thread per (row, restart): threads [g 64, g 64 + 64) of a block update
+// restart g of the block's 64 rows (Eq. symhals_update2, columns in order, the
+// shared row routine of the full-X kernel), instantiated for the block's
+// problem width padded to 8, 16, 24 or 32.  The restart's prepared Gram is
+// copied into shared memory (float4 broadcasts in the column loop).
+// F_upd . Y and ||F_upd - F_fix||^2 are summed per row in FP32 and across rows
+// in double-float (warp xor trees), one FP64 atomic per restart and block.
+__global__ void __launch_bounds__(GH_ROWS * GB_MAXR) grouped_hals_kernel(const HalsProb* __restrict__ hp,
+                                                                         const long long* tile_off, int nprob,
+                                                                         float* Fu_all, const float* Ff_all,
+                                                                         const float* Y_all, const float* Gp_all,
+                                                                         double* part, unsigned* err) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float2 wsum[2 * GB_MAXR * (GH_ROWS / 32)];
+  const int p = find_le(tile_off, nprob, (long long)blockIdx.x);
+  const HalsProb P = hp[p];
+  const int k = P.k, R = P.R;
+  const int KM = gh_km(k);
+  const long long tile = blockIdx.x - tile_off[p];
+  float* Gs = sm;                 // [R][KM][KM]
+  float* inv = Gs + R * KM * KM;  // [R][KM]
+  const float alpha = (float)P.alpha;
+  const int tid = threadIdx.x;
+  {
+    const float4* src = reinterpret_cast<const float4*>(Gp_all + P.gp_off);
+    float4* dst = reinterpret_cast<float4*>(sm);
+    for (int e = tid; e < R * (KM * KM + KM) / 4; e += blockDim.x) dst[e] = src[e];
+  }
+  __syncthreads();
+  const int g = tid / GH_ROWS, rr = tid - g * GH_ROWS;
+  const long long row = tile * GH_ROWS + rr;
+  float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
+  if (g < R && row < P.n) {
+    switch (KM) {
+      case 8: grouped_hals_row<8>(P, g, row, Fu_all, Ff_all, Y_all, Gs, inv, alpha, err, trv, ddv); break;
+      case 16: grouped_hals_row<16>(P, g, row, Fu_all, Ff_all, Y_all, Gs, inv, alpha, err, trv, ddv); break;
+      case 24: grouped_hals_row<24>(P, g, row, Fu_all, Ff_all, Y_all, Gs, inv, alpha, err, trv, ddv); break;
+      default: grouped_hals_row<32>(P, g, row, Fu_all, Ff_all, Y_all, Gs, inv, alpha, err, trv, ddv); break;
+    }
+  }
+  // per restart: xor trees over the warp's 32 rows, then the block's row warps
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    gb_df_add(trv.x, trv.y, __shfl_xor_sync(0xffffffffu, trv.x, off), __shfl_xor_sync(0xffffffffu, trv.y, off));
+    gb_df_add(ddv.x, ddv.y, __shfl_xor_sync(0xffffffffu, ddv.x, off), __shfl_xor_sync(0xffffffffu, ddv.y, off));
+  }
+  constexpr int WPR = GH_ROWS / 32;  // warps per restart
+  const int wid = tid >> 5;
+  if ((tid & 31) == 0) {
+    wsum[2 * wid] = trv;
+    wsum[2 * wid + 1] = ddv;
+  }
+  __syncthreads();
+  if (tid < R) {
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    for (int q = 0; q < WPR; ++q) {
+      gb_df_add(a.x, a.y, wsum[2 * (tid * WPR + q)].x, wsum[2 * (tid * WPR + q)].y);
+      gb_df_add(b.x, b.y, wsum[2 * (tid * WPR + q) + 1].x, wsum[2 * (tid * WPR + q) + 1].y);
+    }
+    atomicAdd(part + 2 * (P.pr_off + tid), (double)a.x + (double)a.y);
+    atomicAdd(part + 2 * (P.pr_off + tid) + 1, (double)b.x + (double)b.y);
+  }
+}
+
+// Per-restart Grams of every problem: blocks own 512-row chunks; upper 4x4
+// tiles only; FP32 over 32-row sub-chunks, double-float (FP32 pairs) per
+// thread across them, one FP64 atomic per entry per block (mirrored tiles
+// added to both halves).
+constexpr int GG_CHUNK = 512, GG_SUB = 32, GG_THREADS = 256;
+
+// Upper 4x4 tile number u (row-major over ti <= tj) of a kt x kt tile grid.
+__device__ __forceinline__ void gg_tri(int u, int kt, int& ti, int& tj) {
+  int b = 0;
+  while (u >= kt - b) {
+    u -= kt - b;
+    ++b;
+  }
+  ti = b;
+  tj = b + u;
+}
 
 __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb* __restrict__ hp,
                                                                   const long long* chunk_off, int nprob,
                                                                   const float* F_all, double* Gd_all) {
   __shared__ __align__(16) float Fs[GG_SUB * GB_BN];
-  __shared__ double red[GG_THREADS * 16];
+  __shared__ float2 red[GG_THREADS * 16];
   const int p = find_le(chunk_off, nprob, (long long)blockIdx.x);
   const HalsProb P = hp[p];
   const int k = P.k, R = P.R, RW = R * k;
   const int k4 = (k + 3) & ~3, tk = k4 >> 2;
-  const int T = R * tk * tk;  // 4x4 tiles over all restarts
+  const int tt = tk * (tk + 1) / 2;  // upper 4x4 tiles of one restart
+  const int T = R * tt;              // over all restarts
   const int RG = T >= GG_THREADS ? 1 : GG_THREADS / T;
   const int tid = threadIdx.x;
   const int rg = tid / T;
   const long long r0 = (blockIdx.x - chunk_off[p]) * (long long)GG_CHUNK;
   const long long r1 = min((long long)P.n, r0 + GG_CHUNK);
   const float* F = F_all + P.f_off;
-  double acc[2][16];
+  float2 acc[2][16];
 #pragma unroll
   for (int t = 0; t < 2; ++t)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[t][e] = 0.0;
+    for (int e = 0; e < 16; ++e) acc[t][e] = make_float2(0.f, 0.f);
   for (long long rb = r0; rb < r1; rb += GG_SUB) {
     const int rows = (int)min((long long)GG_SUB, r1 - rb);
     for (int e = tid; e < GG_SUB * RW; e += GG_THREADS) {
@@ -438,8 +545,9 @@ __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb
     for (int t = 0; t < 2; ++t) {
       const int tile = T >= GG_THREADS ? tid + t * GG_THREADS : (t == 0 ? tid % T : T);
       if (tile < T && rg < RG) {
-        const int g = tile / (tk * tk), rem = tile - g * tk * tk;
-        const int ti = rem / tk, tj = rem - ti * tk;
+        const int g = tile / tt;
+        int ti, tj;
+        gg_tri(tile - g * tt, tk, ti, tj);
         float f[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) f[e] = 0.f;
@@ -457,7 +565,7 @@ __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb
             for (int b = 0; b < 4; ++b) f[a * 4 + b] = fmaf(av[a], bv[b], f[a * 4 + b]);
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[t][e] += (double)f[e];
+        for (int e = 0; e < 16; ++e) gb_df_add(acc[t][e].x, acc[t][e].y, f[e], 0.f);
       }
     }
     __syncthreads();
@@ -470,42 +578,60 @@ __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb
     for (int g2 = 0; g2 < RG; ++g2) {
       if (mine && rg == g2)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) red[(tile % GG_THREADS) * 16 + e] = (g2 == 0 ? 0.0 : red[(tile % GG_THREADS) * 16 + e]) + acc[t][e];
+        for (int e = 0; e < 16; ++e) {
+          float2 v = g2 == 0 ? make_float2(0.f, 0.f) : red[(tile % GG_THREADS) * 16 + e];
+          gb_df_add(v.x, v.y, acc[t][e].x, acc[t][e].y);
+          red[(tile % GG_THREADS) * 16 + e] = v;
+        }
       __syncthreads();
     }
     if (mine && rg == 0) {
-      const int g = tile / (tk * tk), rem = tile - g * tk * tk;
-      const int ti = rem / tk, tj = rem - ti * tk;
+      const int g = tile / tt;
+      int ti, tj;
+      gg_tri(tile - g * tt, tk, ti, tj);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int i = ti * 4 + (e >> 2), j = tj * 4 + (e & 3);
-        if (i < k && j < k) atomicAdd(Gd_all + P.g_off + (long long)g * k * k + i * k + j, red[(tile % GG_THREADS) * 16 + e]);
+        if (i < k && j < k) {
+          const float2 v = red[(tile % GG_THREADS) * 16 + e];
+          const double dv = (double)v.x + (double)v.y;
+          double* Gg = Gd_all + P.g_off + (long long)g * k * k;
+          atomicAdd(Gg + i * k + j, dv);
+          if (ti != tj) atomicAdd(Gg + j * k + i, dv);  // the mirrored tile
+        }
       }
     }
     __syncthreads();
   }
 }
 
-__global__ void grouped_objective_kernel(const HalsProb* hp, int nprob, const double* normX2,
-                                         const double* GW, const double* GH, const double* part,
-                                         double* ring, int* cnt, int cap, int PR) {
-  __shared__ int t_sh;
-  if (threadIdx.x == 0) t_sh = *cnt;
-  __syncthreads();
-  const int t = t_sh;
-  for (int pr = threadIdx.x; pr < PR; pr += blockDim.x) {
-    int p = 0;
-    while (p + 1 < nprob && hp[p + 1].pr_off <= pr) ++p;
+// Surrogate objective of every (problem, restart) by the trace trick, one warp
+// each: sum (W^T W) .* (H^T H) over the lanes (FP64, fixed xor tree), plus
+// ||X||^2 - 2 tr + alpha dd.  cnt[0] is the ring slot; the last block to
+// finish (cnt[1] counts the blocks) advances it.
+__global__ void __launch_bounds__(256) grouped_objective_kernel(const HalsProb* hp, int R, const double* normX2,
+                                                                const double* GW, const double* GH,
+                                                                const double* part, double* ring, int* cnt, int cap,
+                                                                int PR) {
+  const int t = cnt[0];
+  const int lane = threadIdx.x & 31;
+  const int pr = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (pr < PR) {
+    const int p = pr / R, g = pr - p * R;  // restarts are uniform over the batch
     const HalsProb& P = hp[p];
-    const int g = pr - P.pr_off, k = P.k;
+    const int k = P.k;
     const long long o = P.g_off + (long long)g * k * k;
     double s = 0.0;
-    for (int e = 0; e < k * k; ++e) s += GW[o + e] * GH[o + e];
-    const double v = normX2[p] + s - 2.0 * part[2 * pr] + P.alpha * part[2 * pr + 1];
-    if (t < cap) ring[(long long)t * PR + pr] = v;
+    for (int e = lane; e < k * k; e += 32) s = fma(GW[o + e], GH[o + e], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0 && t < cap)
+      ring[(long long)t * PR + pr] = normX2[p] + s - 2.0 * part[2 * pr] + P.alpha * part[2 * pr + 1];
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *cnt = t + 1;
+  if (last_block<1>(reinterpret_cast<unsigned*>(cnt + 1)) && threadIdx.x == 0) {
+    cnt[1] = 0;
+    cnt[0] = t + 1;
+  }
 }
 
 // Restart r of problem p: Philox counter (j, i lo, i hi, TAG_INIT), key seed_p + r;
@@ -549,9 +675,11 @@ struct symnmf_batch_ctx {
   std::vector<HalsProb> hp;
   std::vector<long long> ldp, pack_off;
   long long total_rows = 0, total_f = 0, total_g = 0, total_pack = 0, hals_tiles = 0, gram_chunks = 0;
+  long long total_tiles = 0;  // 128-row tiles of the grouped product
   long long total_iters = 0;
   float *H = nullptr, *W = nullptr, *Y = nullptr;
   double* Gd[2] = {nullptr, nullptr};
+  float* Gp = nullptr;  // padded FP32 Grams of the fixed factor for the HALS blocks
   double *part = nullptr, *normX2 = nullptr, *means = nullptr, *ring = nullptr, *scratch = nullptr;
   int* cnt = nullptr;
   unsigned *err = nullptr, *counter = nullptr;
@@ -652,16 +780,14 @@ static cudaError_t launch_grouped(symnmf_batch_t b, int stages, int G, int max_s
 // All products Y_p = X_p F_p of one half sweep.
 static symnmf_status batched_product(symnmf_batch_t b, const float* F_all) {
   if (b->bf16) {
-    const long long tp = b->total_pack;
-    grouped_pack_kernel<<<(unsigned)((tp + 255) / 256), 256, 0, b->st>>>(
-        b->d_hp, b->d_pack_off, b->d_bn, b->d_ldp, b->nprob, tp, F_all, (__nv_bfloat16*)b->pack);
+    grouped_pack_kernel<<<(unsigned)b->hals_tiles, 256, 0, b->st>>>(b->d_hp, b->d_tile_off, b->nprob, b->d_pack_off,
+                                                                   b->d_bn, b->d_ldp, F_all, (__nv_bfloat16*)b->pack);
     count_launches(1);
     BTRY(cudaGetLastError());
     BTRY(launch_grouped(b, b->stages, b->G, b->max_segs));
     ReduceTab tab{b->d_it_off, b->d_gtile_off, b->d_kb, b->d_row_off, b->d_f_off, b->d_width};
-    const long long work = b->total_rows * GB_BN;
-    grouped_reduce_kernel<<<(unsigned)((work + 255) / 256), 256, 0, b->st>>>(
-        tab, b->nprob, b->partials, b->max_segs, b->total_iters, b->G, b->total_rows, b->Y);
+    grouped_reduce_kernel<<<(unsigned)b->total_tiles, 256, 0, b->st>>>(tab, b->nprob, b->partials, b->max_segs,
+                                                                       b->total_iters, b->G, b->Y);
     count_launches(1);
     BTRY(cudaGetLastError());
     return SYMNMF_OK;
@@ -683,9 +809,10 @@ static symnmf_status batched_half(symnmf_batch_t b, int side) {
   const int gfix = side ? 1 : 0, gupd = side ? 0 : 1;
   BTRYS(batched_product(b, Ff));
   BTRY(cudaMemsetAsync(b->part, 0, (size_t)2 * b->PR * sizeof(double), b->st));
-  grouped_hals_kernel<32><<<(unsigned)b->hals_tiles, GH_ROWS, b->hals_smem, b->st>>>(
-      b->d_hp, b->d_tile_off, b->nprob, Fu, Ff, b->Y, b->Gd[gfix], b->part, b->err);
-  count_launches(1);
+  grouped_gram_prep_kernel<<<(unsigned)b->nprob, 256, 0, b->st>>>(b->d_hp, b->Gd[gfix], b->Gp);
+  grouped_hals_kernel<<<(unsigned)b->hals_tiles, GH_ROWS * b->R, b->hals_smem, b->st>>>(
+      b->d_hp, b->d_tile_off, b->nprob, Fu, Ff, b->Y, b->Gp, b->part, b->err);
+  count_launches(2);
   BTRY(cudaGetLastError());
   BTRY(cudaMemsetAsync(b->Gd[gupd], 0, (size_t)b->total_g * sizeof(double), b->st));
   grouped_gram_kernel<<<(unsigned)b->gram_chunks, GG_THREADS, 0, b->st>>>(b->d_hp, b->d_chunk_off, b->nprob,
@@ -693,8 +820,8 @@ static symnmf_status batched_half(symnmf_batch_t b, int side) {
   count_launches(1);
   BTRY(cudaGetLastError());
   if (side == 1) {
-    grouped_objective_kernel<<<1, 256, 0, b->st>>>(b->d_hp, b->nprob, b->normX2, b->Gd[1], b->Gd[0], b->part,
-                                                   b->ring, b->cnt, OBJ_RING, b->PR);
+    grouped_objective_kernel<<<(unsigned)((b->PR * 32 + 255) / 256), 256, 0, b->st>>>(
+        b->d_hp, b->R, b->normX2, b->Gd[1], b->Gd[0], b->part, b->ring, b->cnt, OBJ_RING, b->PR);
     count_launches(1);
     BTRY(cudaGetLastError());
   }
@@ -730,9 +857,8 @@ static symnmf_status autotune(symnmf_batch_t b) {
   double best = 1e30;
   int bi = 0;
   // pack H once so that the product has valid operands
-  const long long tp = b->total_pack;
-  grouped_pack_kernel<<<(unsigned)((tp + 255) / 256), 256, 0, b->st>>>(
-      b->d_hp, b->d_pack_off, b->d_bn, b->d_ldp, b->nprob, tp, b->H, (__nv_bfloat16*)b->pack);
+  grouped_pack_kernel<<<(unsigned)b->hals_tiles, 256, 0, b->st>>>(b->d_hp, b->d_tile_off, b->nprob, b->d_pack_off,
+                                                                 b->d_bn, b->d_ldp, b->H, (__nv_bfloat16*)b->pack);
   count_launches(1);
   for (int c = 0; c < 3; ++c) {
     const int G = (int)std::min<long long>((long long)num_sms() * cands[c].per_sm, b->total_iters);
@@ -798,7 +924,7 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
   std::vector<long long> tile_off(nprob), chunk_off(nprob), row_off(nprob + 1), it_off(nprob), gtile(nprob),
       f_off(nprob);
   std::vector<int> kb(nprob), width(nprob), bn(nprob);
-  long long f = 0, g = 0, rows = 0, tiles = 0, chunks = 0, its = 0, gt = 0, pk = 0;
+  long long f = 0, g = 0, gp = 0, rows = 0, tiles = 0, chunks = 0, its = 0, gt = 0, pk = 0;
   int pr = 0;
   b->ldp.resize(nprob);
   b->pack_off.resize(nprob);
@@ -810,6 +936,7 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
     h.R = restarts;
     h.f_off = f;
     h.g_off = g;
+    h.gp_off = gp;
     h.row_off = rows;
     h.pr_off = pr;
     f_off[p] = f;
@@ -829,6 +956,10 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
     gt += mt;
     f += (long long)q.n * width[p];
     g += (long long)restarts * q.k * q.k;
+    {
+      const int km = q.k <= 8 ? 8 : q.k <= 16 ? 16 : q.k <= 24 ? 24 : 32;
+      gp += (long long)restarts * (km * km + km);
+    }
     rows += q.n;
     tiles += (q.n + GH_ROWS - 1) / GH_ROWS;
     chunks += (q.n + GG_CHUNK - 1) / GG_CHUNK;
@@ -836,13 +967,9 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
     b->hp.push_back(h);
   }
   row_off[nprob] = rows;
-  // grouped HALS: R k x k Grams, R k inverses, Y / H / W tiles of 64 padded rows
-  for (int p = 0; p < nprob; ++p) {
-    const int k = probs[p].k, RW = restarts * k;
-    const size_t need = (size_t)(restarts * k * k + restarts * k + 3 * GH_ROWS * (RW + 1)) * sizeof(float);
-    b->hals_smem = std::max(b->hals_smem, need);
-  }
-  if (cudaFuncSetAttribute(grouped_hals_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // grouped HALS: R zero-padded (at most 32 x 32) Grams and R x 32 inverses
+  b->hals_smem = (size_t)restarts * (32 * 32 + 32) * sizeof(float);
+  if (cudaFuncSetAttribute(grouped_hals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)b->hals_smem) != cudaSuccess)
     return bail(SYMNMF_ECUDA);
   b->PR = pr;
@@ -852,6 +979,7 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
   b->hals_tiles = tiles;
   b->gram_chunks = chunks;
   b->total_iters = its;
+  b->total_tiles = gt;
   b->total_pack = pk;
 #define BA(ptr, cnt)                                           \
   do {                                                         \
@@ -862,6 +990,7 @@ extern "C" symnmf_status symnmf_batched_create(const symnmf_problem* probs, int 
   BA(b->Y, f);
   BA(b->Gd[0], g);
   BA(b->Gd[1], g);
+  BA(b->Gp, gp);
   BA(b->part, 2 * pr);
   BA(b->normX2, nprob);
   BA(b->means, nprob);
@@ -1016,7 +1145,7 @@ extern "C" symnmf_status symnmf_batched_sweep(symnmf_batch_t b, int nsweeps, dou
   bool warmed = false;
   while (done < nsweeps) {
     const int chunk = std::min(nsweeps - done, OBJ_RING);
-    BTRY(cudaMemsetAsync(b->cnt, 0, 4, b->st));
+    BTRY(cudaMemsetAsync(b->cnt, 0, 8, b->st));  // ring slot, finished-block count
     int t = 0;
     if (!warmed) {
       BTRYS(batched_body(b));

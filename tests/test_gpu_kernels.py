@@ -151,6 +151,28 @@ def test_csr_product(S):
         np.testing.assert_allclose(Y, ref, rtol=2e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("n,N", [(270001, 64), (1100003, 20), (2500003, 10), (4000001, 5)])
+def test_csr_product_with_f_larger_than_l2(S, n, N):
+    # F of 64 to 95 MB: the gathers of F rows miss L2; every width path (N = 5, 10: half a warp
+    # per row, 20: a warp, 64: float2 loads) against the exact product of the FP32 operands
+    rng = np.random.default_rng(n)
+    deg = 6
+    rows = np.repeat(np.arange(n), deg)
+    cols = rng.integers(0, n, size=n * deg)
+    Xs = sp.csr_matrix((rng.random(n * deg), (rows, cols)), shape=(n, n))
+    Xs.sum_duplicates()
+    Xs.sort_indices()
+    F = rng.random((n, N)).astype(np.float32)
+    rp = torch.tensor(Xs.indptr.astype(np.int64), device="cuda")
+    col = torch.tensor(Xs.indices.astype(np.int32), device="cuda")
+    val = torch.tensor(Xs.data.astype(np.float32), device="cuda")
+    Y = np64(S.csr_xf(rp, col, val, t32(F)))
+    Xe = sp.csr_matrix((Xs.data.astype(np.float32).astype(np.float64), Xs.indices, Xs.indptr), shape=(n, n))
+    ref = Xe @ F.astype(np.float64)
+    bound = 2e-6 * (abs(Xe) @ np.abs(F.astype(np.float64))) + 1e-30
+    assert (np.abs(Y - ref) <= bound).all(), np.abs(Y - ref).max()
+
+
 @pytest.mark.parametrize("n,N", [(1, 3), (50, 10), (20000, 64), (100003, 20), (3000, 96)])
 def test_gram_fp64_accumulation(S, n, N):
     F = uniform_factor(n, N, seed=n).astype(np.float32).astype(np.float64)
