@@ -62,7 +62,11 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
   static constexpr int B_STAGES = WIDE ? 2 : M2 ? 3 : 4;
-  static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
+  // X stages fill what the F^T stages leave of the budget: 224 KB for the HBM-bound
+  // narrow tiles (measured 0.81 -> 0.825 of HBM at N = 20/50), 200 KB for the wide ones
+  // (a fourth 256-row X stage lowered N = 256 from 0.66 to 0.65 of the tensor peak)
+  static constexpr int BUDGET = (!M2 && BN <= 128 ? 224 : 200) * 1024;
+  static constexpr int A_FIT = (BUDGET - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
   // accumulator buffers in TMEM: four alternate, so that the epilogue's drains
   // of short accumulations never hold up the MMAs
@@ -76,6 +80,7 @@ struct TcCfg {
   static constexpr uint32_t TMEM_COLS = M2 ? 2 * BN : (NBUF * BN < 32 ? 32 : NBUF * BN);
   static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
   static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
+  static_assert(SMEM <= 227 * 1024, "dynamic shared memory above the opt-in limit");
 };
 
 template <int BN, bool FP8, bool M2 = false>
