@@ -62,11 +62,9 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
   static constexpr int B_STAGES = WIDE ? 2 : M2 ? 3 : 4;
-  // X stages fill what the F^T stages leave of the budget: 224 KB for the HBM-bound
-  // narrow tiles (measured 0.81 -> 0.825 of HBM at N = 20/50), 200 KB for the wide ones
-  // (a fourth 256-row X stage lowered N = 256 from 0.66 to 0.65 of the tensor peak)
-  static constexpr int BUDGET = (!M2 && BN <= 128 ? 224 : 200) * 1024;
-  static constexpr int A_FIT = (BUDGET - B_STAGES * B_BYTES) / A_BYTES;
+  // X stages fill what the F^T stages leave of 200 KB (at most 10).  A 224 KB budget (a
+  // fourth 256-row X stage) measured slower at N = 256 (0.66 -> 0.65 of the tensor peak).
+  static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
   // accumulator buffers in TMEM: four alternate, so that the epilogue's drains
   // of short accumulations never hold up the MMAs
