@@ -125,6 +125,11 @@ __global__ void __launch_bounds__(RS_THREADS) xf_rows_kernel(const float* __rest
       reinterpret_cast<float*>(Fs)[e] = (kk < kc && c < N) ? F[(k0 + kk) * ldf + c] : 0.f;
     }
     __syncthreads();
+    // the next step's X values are loaded one step ahead (registers), so that
+    // their load latency overlaps the current step's FMAs
+    float4 xn[RS_RT];
+#pragma unroll
+    for (int i = 0; i < RS_RT; ++i) xn[i] = __ldg(reinterpret_cast<const float4*>(xr[i] + k0));
     for (int kk = 0; kk < kc; kk += 4) {  // kc is a multiple of 4 (n % 4 == 0)
       if (((k0 + kk) & 31) == 0 && k0 + kk + 32 < kend)
 #pragma unroll
@@ -132,7 +137,10 @@ __global__ void __launch_bounds__(RS_THREADS) xf_rows_kernel(const float* __rest
           asm volatile("prefetch.global.L1 [%0];" ::"l"(xr[i] + k0 + kk + 32));
       float4 x[RS_RT];
 #pragma unroll
-      for (int i = 0; i < RS_RT; ++i) x[i] = __ldg(reinterpret_cast<const float4*>(xr[i] + k0 + kk));
+      for (int i = 0; i < RS_RT; ++i) x[i] = xn[i];
+      if (kk + 4 < kc)
+#pragma unroll
+        for (int i = 0; i < RS_RT; ++i) xn[i] = __ldg(reinterpret_cast<const float4*>(xr[i] + k0 + kk + 4));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
 #pragma unroll

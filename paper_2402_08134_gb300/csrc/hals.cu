@@ -20,6 +20,14 @@ constexpr int hals_ns() {
   return 1;
 }
 
+// Widths at which the column loop runs rolled, in rotating blocks of 16
+// (hals_row_rotating): the fully unrolled 64-column body misses the
+// instruction cache.
+template <int KMAX>
+constexpr bool hals_rot() {
+  return KMAX >= 48;
+}
+
 // Full-X HALS update, Eq. symhals_update2:
 //   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
 // i = 0..k-1 in order with the columns already updated.  NS = hals_ns threads
@@ -36,7 +44,8 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
     const float* __restrict__ Y, int ldy, const float* __restrict__ U, int l, const float* __restrict__ M,
     double* part, double* ws, unsigned* counter, unsigned* err) {
   constexpr int NS = hals_ns<KMAX>(), KH = KMAX / NS;
-  constexpr int RS = hals_split_stride<KMAX, NS>();
+  constexpr bool ROT = hals_rot<KMAX>();
+  constexpr int RS = ROT ? 2 * KMAX : hals_split_stride<KMAX, NS>();
   constexpr int RPB = HALS_THREADS / NS;  // rows per block and pass
   extern __shared__ __align__(16) float sm[];
   float* Gs = sm;               // KMAX x RS, diagonal zeroed
@@ -47,7 +56,9 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
   for (int e = tid; e < KMAX * KMAX; e += HALS_THREADS) {
     const int i = e / KMAX, j = e - i * KMAX;
     const int part = j / KH;
-    Gs[i * RS + part * (NS > 1 ? KH + 4 : KH) + (j - part * KH)] = (i < k && j < k && i != j) ? G[i * k + j] : 0.f;
+    const float v = (i < k && j < k && i != j) ? G[i * k + j] : 0.f;
+    Gs[i * RS + part * (NS > 1 ? KH + 4 : KH) + (j - part * KH)] = v;
+    if constexpr (ROT) Gs[i * RS + KMAX + j] = v;  // each row twice (rotated reads)
   }
   if (U)
     for (int e = tid; e < l * KMAX; e += HALS_THREADS) {
@@ -115,9 +126,14 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
     }
     // the fixed row is read column by column (L1 hits after the first); the
     // shared-memory column of Y is this thread's own, so no barrier is needed
-    bad |= hals_row_split<KMAX, NS>(
-        w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, p, mask, Gp4, inv,
-        [&](int c) { return __ldg(fx + c); }, trv, ddv);
+    if constexpr (ROT)
+      bad |= hals_row_rotating<KMAX, 16>(
+          w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, Gs, inv, [&](int c) { return __ldg(fx + c); },
+          trv, ddv);
+    else
+      bad |= hals_row_split<KMAX, NS>(
+          w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, p, mask, Gp4, inv,
+          [&](int c) { return __ldg(fx + c); }, trv, ddv);
     if constexpr (VEC) {
 #pragma unroll
       for (int q = 0; q < KH / 4; ++q)
@@ -147,8 +163,8 @@ template <int KMAX, bool VEC>
 static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, const float* G, double alpha,
                                const float* Y, int ldy, const float* U, int l, const float* M, double* part,
                                double* ws, unsigned* counter, unsigned* err, cudaStream_t st) {
-  size_t smem = (size_t)(KMAX * hals_split_stride<KMAX, hals_ns<KMAX>()>() + KMAX +
-                         (KMAX / hals_ns<KMAX>()) * HALS_THREADS) * 4;
+  const int rs = hals_rot<KMAX>() ? 2 * KMAX : hals_split_stride<KMAX, hals_ns<KMAX>()>();
+  size_t smem = (size_t)(KMAX * rs + KMAX + (KMAX / hals_ns<KMAX>()) * HALS_THREADS) * 4;
   if (U) smem += (size_t)l * KMAX * 4;
   auto kern = hals_kernel<KMAX, VEC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -130,4 +130,57 @@ __device__ __forceinline__ bool hals_row_split(float (&w)[KMAX / NS], YA y_at, f
   return bad;
 }
 
+// The same rule for one row held by one thread, with the column loop rolled in
+// blocks of BB columns so that the code stays small at large widths (the fully
+// unrolled 64-column body overflows the instruction cache): before block b the
+// registers w hold the row rotated left by b BB columns, so the block's columns
+// are always w[0..BB) (static register indices); G is read from rows stored
+// twice side by side (row stride 2 KMAX, diagonal zeroed), starting at column
+// b BB, which lines G up with the rotated w.  After the last block w is back in
+// order.  Same arithmetic per column as hals_row_split with NS = 1 (four FMA
+// chains), summed in the rotated order.
+template <int KMAX, int BB, class YA, class FXA>
+__device__ __forceinline__ bool hals_row_rotating(float (&w)[KMAX], YA y_at, float alpha, int k, const float* Gd,
+                                                  const float* inv, FXA fx_at, float2& trv, float2& ddv) {
+  static_assert(KMAX % BB == 0 && BB % 4 == 0 && BB % 2 == 0, "blocks of whole float4 runs");
+  bool bad = false;
+  float t[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};
+#pragma unroll 1
+  for (int b = 0; b < KMAX / BB; ++b) {
+#pragma unroll
+    for (int ii = 0; ii < BB; ++ii) {
+      const int i = b * BB + ii;
+      const float4* g4 = reinterpret_cast<const float4*>(Gd + (size_t)i * 2 * KMAX + b * BB);
+      float ac[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j4 = 0; j4 < KMAX / 4; ++j4) {
+        const float4 g = g4[j4];
+        ac[0] = fmaf(-w[4 * j4 + 0], g.x, ac[0]);
+        ac[1] = fmaf(-w[4 * j4 + 1], g.y, ac[1]);
+        ac[2] = fmaf(-w[4 * j4 + 2], g.z, ac[2]);
+        ac[3] = fmaf(-w[4 * j4 + 3], g.w, ac[3]);
+      }
+      const float s = (ac[0] + ac[1]) + (ac[2] + ac[3]);
+      const float hi = i < k ? fx_at(i) : 0.f;
+      const float yi = y_at(i);
+      const float wi = fmaxf((yi + fmaf(alpha, hi, s)) * inv[i], 0.f);  // padded columns: inv = 0
+      w[ii] = wi;
+      if (!isfinite(wi)) bad = true;
+      const float d = wi - hi;
+      t[ii & 1] = fmaf(wi, yi, t[ii & 1]);
+      d2[ii & 1] = fmaf(d, d, d2[ii & 1]);
+    }
+    float head[BB];
+#pragma unroll
+    for (int q = 0; q < BB; ++q) head[q] = w[q];
+#pragma unroll
+    for (int j = 0; j < KMAX - BB; ++j) w[j] = w[j + BB];
+#pragma unroll
+    for (int q = 0; q < BB; ++q) w[KMAX - BB + q] = head[q];
+  }
+  hr_df_add(trv, t[0] + t[1]);
+  hr_df_add(ddv, d2[0] + d2[1]);
+  return bad;
+}
+
 }  // namespace symnmf
