@@ -18,8 +18,9 @@
 // at most 8 k blocks and the epilogue adds a row tile's accumulations in FP32
 // registers (round to nearest), which keeps the tensor core's per-MMA
 // accumulation drift (~2e-8 relative, low) from building up over long K.
-// Wider products (256 columns on 256-row tiles, 512 columns) fill TMEM with
-// one accumulator per segment and keep that drift (~6e-5 at K = 20000).
+// Wider products (256 columns on 256-row tiles; 512 columns on CTA pairs, see
+// xf_tc2_kernel) fill TMEM with one accumulator per segment and keep that
+// drift (~6e-5 at K = 20000).
 //
 // Work split (stream-K): the (row tile, k block) iteration space is cut into
 // gridDim.x equal contiguous ranges, one per CTA, so every SM streams the
@@ -49,19 +50,17 @@ constexpr int XF_THREADS = 224;  // warps 0..6: A producer, MMA, 4 epilogue warp
 
 // M2: a CTA's row tile is 256 rows (two 128-row MMA halves sharing every F
 // stage, accumulators in TMEM columns [0, BN) and [BN, 2 BN), one buffer);
-// otherwise 128 rows.  BN = 512 (128 rows): each k step issues two N = 256
-// MMAs into TMEM columns [0, 256) and [256, 512), one buffer; each F stage is
-// two 256-row TMA boxes.
+// otherwise 128 rows.  (512 columns run on CTA pairs: xf_tc2_kernel.)
 template <int BN, bool M2 = false>
 struct TcCfg {
+  static_assert(BN <= 256, "512 columns run on CTA pairs");
   static constexpr int BM = M2 ? 2 * TC_BM : TC_BM;
-  static constexpr bool WIDE = BN > 256;
-  static constexpr int MMA_N = WIDE ? 256 : BN;     // columns per MMA
-  static constexpr int NB_MMA = BN / MMA_N;         // MMAs per k step and row half
+  static constexpr int MMA_N = BN;                  // columns per MMA
+  static constexpr int NB_MMA = 1;                  // MMAs per k step and row half
   static constexpr bool REGACC = !M2 && BN <= 128;  // epilogue adds accumulations in registers
   static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
-  static constexpr int B_STAGES = WIDE ? 2 : M2 ? 3 : 4;
+  static constexpr int B_STAGES = M2 ? 3 : 4;
   // X stages fill what the F^T stages leave of 200 KB (at most 10).  A 224 KB budget (a
   // fourth 256-row X stage) measured slower at N = 256 (0.66 -> 0.65 of the tensor peak).
   static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
@@ -338,6 +337,200 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
                  : "memory");
 }
 
+// 512 columns on CTA pairs (cta_group::2).  A pair of CTAs on two SMs (a
+// cluster of 2) shares each 256-row X tile: CTA r holds rows [128 r, 128 r +
+// 128) of the tile and, of each of the two N = 256 MMAs per k step, F^T rows
+// [256 j + 128 r, 256 j + 128 r + 128); the leader (rank 0) issues the pair's
+// MMAs (M = 256), which read both CTAs' shared memory and leave each CTA's 128
+// rows x 512 columns in its own TMEM.  Per CTA and k block that is 16 KB of X
+// and 32 KB of F^T against 4.2 M MACs, where one CTA alone on a 128-row tile
+// needs 64 KB of F^T for the same work: the L2 stream of F^T that bounds the
+// single-CTA tile halves.  Both CTAs' TMA copies complete on the leader's
+// stage barrier; the leader's commits arrive on both CTAs' "stage free" and
+// "accumulator full" barriers; both CTAs' epilogue warps arrive on the
+// leader's "accumulator free" barrier.  Waits are bounded as in xf_tc_kernel;
+// every thread of both CTAs reaches the final cluster barrier.
+constexpr int TC2_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer (leader), warps 2..5 epilogue
+constexpr int TC2_BN = 512;
+constexpr int TC2_A_BYTES = TC_BM * TC_ROW_BYTES;          // this CTA's 128 rows of X
+constexpr int TC2_B_BYTES = 2 * TC_BM * TC_ROW_BYTES;      // this CTA's half of each MMA's F^T
+constexpr int TC2_STAGE = TC2_A_BYTES + TC2_B_BYTES;       // 48 KB
+constexpr int TC2_STAGES = 4;
+constexpr int TC2_SMEM = TC2_STAGES * TC2_STAGE + 1024 + 512;
+static_assert(TC2_SMEM <= 227 * 1024, "dynamic shared memory above the opt-in limit");
+
+template <bool FP8>
+__global__ void __launch_bounds__(TC2_THREADS, 1)
+    xf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kblocks,
+                  int64_t total_iters, float* __restrict__ partials, int max_segs, unsigned* err) {
+  constexpr int KELEMS = FP8 ? 128 : 64;  // elements of K per k block
+  constexpr int KSTEPS = TC_ROW_BYTES / 32;
+  constexpr uint32_t IDESC = make_idesc<FP8>(2 * TC_BM, 256);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + TC2_STAGES * TC2_STAGE);
+  uint64_t* empty = full + TC2_STAGES;
+  uint64_t* tfull = empty + TC2_STAGES;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* done = tempty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int64_t it0 = ((int64_t)pair * total_iters) / npairs;
+  const int64_t it1 = ((int64_t)(pair + 1) * total_iters) / npairs;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC2_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 8);  // 4 epilogue warps in each CTA (the leader's barrier is the one used)
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {  // both CTAs take part in the pair's allocation
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_parity = 0;
+      for (int64_t it = it0; it < it1; ++it) {
+        const int64_t tile = it / kblocks;
+        const int kb = (int)(it - tile * kblocks);
+        if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          set_error(err, ERR_TIMEOUT);
+          break;
+        }
+        if (rank == 0) mbar_expect_tx(&full[stage], 2 * TC2_STAGE);  // both CTAs' copies
+        const uint32_t bar_cl = map_to_rank(smem_u32(&full[stage]), 0);
+        uint8_t* sA = smem + stage * TC2_STAGE;
+        uint8_t* sB = sA + TC2_A_BYTES;
+        tma_load_2d_pair(sA, &tmA, kb * KELEMS, (int)(tile * 2 * TC_BM + rank * TC_BM), bar_cl);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          tma_load_2d_pair(sB + j * TC_BM * TC_ROW_BYTES, &tmB, kb * KELEMS, (int)(256 * j + rank * TC_BM), bar_cl);
+        issued_mask |= 1u << stage;
+        last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+        if (++stage == TC2_STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      // the leader's stage barriers count both CTAs' copies: every copy issued
+      // has landed once they complete
+      if (rank == 0)
+        for (int s = 0; s < TC2_STAGES; ++s)
+          if (issued_mask >> s & 1u) {
+            volatile int no_abort = 0;
+            mbar_wait_cl(&full[s], (last_parity >> s) & 1u, &no_abort);
+          }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      int sa = 0, seg = 0;
+      uint32_t pa = 0;
+      bool ok = true;
+      int64_t it = it0;
+      while (ok && it < it1) {
+        const int64_t tile = it / kblocks;
+        const int64_t seg_end = min(it1, (tile + 1) * kblocks);
+        if (!mbar_wait_cl(tempty, ((uint32_t)seg & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t seg_begin = it;
+        for (; it < seg_end; ++it) {
+          if (!mbar_wait_cl(&full[sa], pa, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + sa * TC2_STAGE);
+          const uint32_t b0 = a0 + TC2_A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ++ks)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+              umma_pair<FP8>(tmem_base + (uint32_t)(j * 256), sw128_desc(a0 + ks * 32),
+                             sw128_desc(b0 + j * TC_BM * TC_ROW_BYTES + ks * 32), IDESC,
+                             (it > seg_begin || ks > 0) ? 1u : 0u);
+          umma_commit_pair(&empty[sa], 3);
+          if (++sa == TC2_STAGES) {
+            sa = 0;
+            pa ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit_pair(tfull, 3);
+        ++seg;
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        set_error(err, ERR_TIMEOUT);
+      }
+      // all MMAs of the pair complete before either CTA releases its TMEM
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(done))
+                   : "memory");
+      volatile int no_abort = 0;
+      mbar_wait_cl(done, 0, &no_abort);
+    }
+  } else {
+    // epilogue: this CTA's 128 rows (its TMEM lanes) x 512 columns per segment
+    const int ew = warp & 3;
+    int seg = 0;
+    int64_t it = it0;
+    const uint32_t tempty_leader = map_to_rank(smem_u32(tempty), 0);
+    while (it < it1) {
+      const int64_t tile = it / kblocks;
+      const int64_t seg_end = min(it1, (tile + 1) * kblocks);
+      if (!mbar_wait_cl(tfull, (uint32_t)seg & 1u, abort_flag)) {
+        *abort_flag = 1;
+        set_error(err, ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int row = (int)rank * TC_BM + ew * 32 + lane;
+      float* dst = partials + (((size_t)pair * max_segs + seg) * 2 * TC_BM + row) * TC2_BN;
+      const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < TC2_BN; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)c, v);
+#pragma unroll
+        for (int q = 0; q < 16; q += 4) *(float4*)(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_remote(tempty_leader);
+      it = seg_end;
+      ++seg;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+}
+
 // Y[r, c] = (sum over the CTAs that covered row tile r / 128 of their partial)
 //           * row_scale[r] * col_scale[c]  (scales for FP8 only).
 __global__ void tc_reduce_kernel(const float* __restrict__ partials, int max_segs, int BN, int BM, int kblocks,
@@ -420,14 +613,17 @@ struct TcPlan {
 // products, where F's traffic from L2 would otherwise limit the tensor rate.
 static bool tc_m2(int N) { return N > 128 && N <= 256; }
 
-static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM) {
+// 512 columns: CTA pairs on 256-row tiles (G counts pairs).
+static bool tc_pair(int N) { return N > 256; }
+
+static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM, bool pairs = false) {
   TcPlan p;
   const int kel = fp8 ? 128 : 64;
   p.bm = bm;
   p.kblocks = (int)((kdim + kel - 1) / kel);
   p.mtiles = (int)((m + bm - 1) / bm);
   p.total = (int64_t)p.kblocks * p.mtiles;
-  p.G = (int)std::min<int64_t>(num_sms(), p.total);
+  p.G = (int)std::min<int64_t>(pairs ? num_sms() / 2 : num_sms(), p.total);
   p.max_segs = 1;
   for (int c = 0; c < p.G; ++c) {
     const int64_t a = ((int64_t)c * p.total) / p.G, b = ((int64_t)(c + 1) * p.total) / p.G;
@@ -439,10 +635,11 @@ static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM) {
 
 size_t tc_gemm_ws_floats(int64_t m, int64_t kdim, int BN) {
   // largest of the plans a product of this width can use
-  const int bm = tc_m2(BN) ? 2 * TC_BM : TC_BM;
+  const bool pairs = tc_pair(BN);
+  const int bm = (tc_m2(BN) || pairs) ? 2 * TC_BM : TC_BM;
   size_t need = 0;
   for (int f = 0; f < 2; ++f) {
-    const TcPlan p = tc_plan(m, kdim, f != 0, bm);
+    const TcPlan p = tc_plan(m, kdim, f != 0, bm, pairs);
     need = std::max(need, (size_t)p.G * p.max_segs * bm * BN);
   }
   return need;
@@ -514,6 +711,28 @@ cudaError_t pack_ft_fp8(const float* F, int64_t n, int ldf, int N, int Npad, voi
   return cudaGetLastError();
 }
 
+template <bool FP8>
+static cudaError_t launch_tc2(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
+                              unsigned* err, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(xf_tc2_kernel<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * p.G));
+  cfg.blockDim = dim3(TC2_THREADS);
+  cfg.dynamicSmemBytes = TC2_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, xf_tc2_kernel<FP8>, ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  count_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <int BN, bool FP8, bool M2 = false>
 static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
                              unsigned* err, cudaStream_t st) {
@@ -545,15 +764,15 @@ cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, c
   // TMA: 16-byte aligned bases and row pitches
   if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
     return cudaErrorInvalidValue;
-  const bool m2 = tc_m2(N);
-  const TcPlan p = tc_plan(m, n, fp8, m2 ? 2 * TC_BM : TC_BM);
+  const bool m2 = tc_m2(N), pairs = tc_pair(N);
+  const TcPlan p = tc_plan(m, n, fp8, (m2 || pairs) ? 2 * TC_BM : TC_BM, pairs);
   if (ws_floats < (size_t)p.G * p.max_segs * p.bm * BN) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   const uint32_t kel = fp8 ? 128 : 64;
   if (!tc_make_map(&ma, X, fp8, (uint64_t)n, (uint64_t)m, (uint64_t)ldx * es, kel, TC_BM))
     return cudaErrorInvalidValue;
   if (!tc_make_map(&mb, Fpack, fp8, (uint64_t)n, (uint64_t)BN, (uint64_t)ldp * es, kel,
-                   (uint32_t)(BN > 256 ? 256 : BN)))
+                   (uint32_t)(pairs ? TC_BM : BN)))
     return cudaErrorInvalidValue;
   cudaError_t e;
   if (ev_begin) cudaEventRecord(ev_begin, st);
@@ -563,7 +782,7 @@ cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, c
       case 64: e = launch_tc<64, true>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, true>(ma, mb, p, ws, err, st); break;
       case 256: e = launch_tc<256, true, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<512, true>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc2<true>(ma, mb, p, ws, err, st); break;
     }
   } else {
     switch (BN) {
@@ -571,7 +790,7 @@ cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, c
       case 64: e = launch_tc<64, false>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, false>(ma, mb, p, ws, err, st); break;
       case 256: e = launch_tc<256, false, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc<512, false>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc2<false>(ma, mb, p, ws, err, st); break;
     }
   }
   if (ev_end) cudaEventRecord(ev_end, st);
