@@ -1,8 +1,8 @@
 // Dense Y = X F on the 5th-generation tensor cores (tcgen05) for BF16 or FP8
 // (E4M3, per-row scales of X and per-column scales of F) X, FP32 accumulation
-// in tensor memory.  This is the product that dominates SymNMF
-// ("products with X are the most expensive part", Section "Complexity" of
-// the LvS section) and the range finder of Alg. RRF.
+// in tensor memory.  This is the product whose O(n^2 k) cost dominates a
+// SymNMF sweep (the complexity discussion of the LvS section) and the range
+// finder of Alg. RRF.
 //
 // Layout: A = X (n x n, K-major rows, TMA tiles 128 x 128 bytes, 128-byte
 // swizzle), B = F^T packed (BN x n, K-major, same swizzle), D = 128 x BN FP32
@@ -18,9 +18,9 @@
 // at most 8 k blocks and the epilogue adds a row tile's accumulations in FP32
 // registers (round to nearest), which keeps the tensor core's per-MMA
 // accumulation drift (~2e-8 relative, low) from building up over long K.
-// Wider products (256 columns on 256-row tiles; 512 columns on CTA pairs, see
-// xf_tc2_kernel) fill TMEM with one accumulator per segment and keep that
-// drift (~6e-5 at K = 20000).
+// Wider products (more than 128 columns) run on CTA pairs (xf_tc2_kernel):
+// they fill TMEM with one accumulator per segment and keep that drift
+// (~6e-5 at K = 20000).
 //
 // Work split (stream-K): the (row tile, k block) iteration space is cut into
 // gridDim.x equal contiguous ranges, one per CTA, so every SM streams the
@@ -48,44 +48,41 @@ namespace symnmf {
 
 constexpr int XF_THREADS = 224;  // warps 0..6: A producer, MMA, 4 epilogue warps, B producer
 
-// M2: a CTA's row tile is 256 rows (two 128-row MMA halves sharing every F
-// stage, accumulators in TMEM columns [0, BN) and [BN, 2 BN), one buffer);
-// otherwise 128 rows.  (512 columns run on CTA pairs: xf_tc2_kernel.)
-template <int BN, bool M2 = false>
+// One CTA per 128-row tile, up to 128 columns (wider products run on CTA
+// pairs: xf_tc2_kernel).
+template <int BN>
 struct TcCfg {
-  static_assert(BN <= 256, "512 columns run on CTA pairs");
-  static constexpr int BM = M2 ? 2 * TC_BM : TC_BM;
+  static_assert(BN <= 128, "wider products run on CTA pairs");
+  static constexpr int BM = TC_BM;
   static constexpr int MMA_N = BN;                  // columns per MMA
-  static constexpr int NB_MMA = 1;                  // MMAs per k step and row half
-  static constexpr bool REGACC = !M2 && BN <= 128;  // epilogue adds accumulations in registers
+  static constexpr int NB_MMA = 1;                  // MMAs per k step
+  static constexpr bool REGACC = true;              // epilogue adds accumulations in registers
   static constexpr int A_BYTES = BM * TC_ROW_BYTES;
   static constexpr int B_BYTES = BN * TC_ROW_BYTES;
-  static constexpr int B_STAGES = M2 ? 3 : 4;
-  // X stages fill what the F^T stages leave of 200 KB (at most 10).  A 224 KB budget (a
-  // fourth 256-row X stage) measured slower at N = 256 (0.66 -> 0.65 of the tensor peak).
+  static constexpr int B_STAGES = 4;
+  // X stages fill what the F^T stages leave of 200 KB (at most 10).
   static constexpr int A_FIT = (200 * 1024 - B_STAGES * B_BYTES) / A_BYTES;
   static constexpr int A_STAGES = A_FIT > 10 ? 10 : A_FIT;
   // accumulator buffers in TMEM: four alternate, so that the epilogue's drains
   // of short accumulations never hold up the MMAs
-  static constexpr int NBUF = REGACC ? 4 : 1;
+  static constexpr int NBUF = 4;
   // k blocks accumulated in TMEM before the epilogue adds them into FP32
   // registers (round to nearest): the tensor core's accumulation drifts low by
   // a fraction of an FP32 ulp per MMA, which over a whole 20000-long K range
-  // biased X F by ~7e-5 relative.  256-row tiles keep one accumulation per
-  // segment (their single TMEM buffer has no room to alternate).
-  static constexpr int64_t CHUNK = REGACC ? XF_TC_CHUNK : (int64_t)1 << 40;
-  static constexpr uint32_t TMEM_COLS = M2 ? 2 * BN : (NBUF * BN < 32 ? 32 : NBUF * BN);
+  // biased X F by ~7e-5 relative.
+  static constexpr int64_t CHUNK = XF_TC_CHUNK;
+  static constexpr uint32_t TMEM_COLS = NBUF * BN < 32 ? 32 : NBUF * BN;
   static_assert(TMEM_COLS <= 512, "TMEM holds 512 columns");
   static constexpr int SMEM = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 512;
   static_assert(SMEM <= 227 * 1024, "dynamic shared memory above the opt-in limit");
 };
 
-template <int BN, bool FP8, bool M2 = false>
+template <int BN, bool FP8>
 __global__ void __launch_bounds__(XF_THREADS, 1)
     xf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int kblocks, int64_t total_iters, float* __restrict__ partials, int max_segs,
                  unsigned* err) {
-  using C = TcCfg<BN, M2>;
+  using C = TcCfg<BN>;
   constexpr int BM = C::BM, NBUF = C::NBUF;
   constexpr int SA = C::A_STAGES, SB = C::B_STAGES;
   constexpr int KSTEPS = TC_ROW_BYTES / 32;  // 32 bytes of K per MMA (16 bf16 / 32 e4m3)
@@ -296,37 +293,6 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
         ++seg;
       }
     }
-    while (!C::REGACC && it < it1) {
-      const int64_t tile = it / kblocks;
-      const int64_t seg_end = min(it1, (tile + 1) * kblocks);
-      const int a = seg % NBUF;
-      const uint32_t use = (uint32_t)(seg / NBUF);
-      if (!mbar_wait(&tfull[a], use & 1u, abort_flag)) {
-        *abort_flag = 1;
-        set_error(err, ERR_TIMEOUT);
-        break;
-      }
-      tc_fence_after();
-#pragma unroll 1
-      for (int h = 0; h < BM / TC_BM; ++h) {
-        const int row = h * TC_BM + ew * 32 + lane;
-        float* dst = partials + (((size_t)blockIdx.x * max_segs + seg) * BM + row) * BN;
-        const uint32_t taddr = tmem_base + ((uint32_t)(ew * 32) << 16) + (uint32_t)((a + h) * BN);
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-          float v[16];
-          tmem_ld16(taddr + (uint32_t)c, v);
-#pragma unroll
-          for (int q = 0; q < 16; q += 4)
-            *(float4*)(dst + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[a]);
-      it = seg_end;
-      ++seg;
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -351,18 +317,25 @@ __global__ void __launch_bounds__(XF_THREADS, 1)
 // leader's "accumulator free" barrier.  Waits are bounded as in xf_tc_kernel;
 // every thread of both CTAs reaches the final cluster barrier.
 constexpr int TC2_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer (leader), warps 2..5 epilogue
-constexpr int TC2_BN = 512;
-constexpr int TC2_A_BYTES = TC_BM * TC_ROW_BYTES;          // this CTA's 128 rows of X
-constexpr int TC2_B_BYTES = 2 * TC_BM * TC_ROW_BYTES;      // this CTA's half of each MMA's F^T
-constexpr int TC2_STAGE = TC2_A_BYTES + TC2_B_BYTES;       // 48 KB
-constexpr int TC2_STAGES = 4;
-constexpr int TC2_SMEM = TC2_STAGES * TC2_STAGE + 1024 + 512;
-static_assert(TC2_SMEM <= 227 * 1024, "dynamic shared memory above the opt-in limit");
 
-template <bool FP8>
+// NB N = 256 MMAs per k step: 256 (NB = 1) or 512 (NB = 2) columns.
+template <int NB>
+struct Tc2Cfg {
+  static constexpr int BN = 256 * NB;
+  static constexpr int A_BYTES = TC_BM * TC_ROW_BYTES;        // this CTA's 128 rows of X
+  static constexpr int B_BYTES = NB * TC_BM * TC_ROW_BYTES;   // this CTA's half of each MMA's F^T
+  static constexpr int STAGE = A_BYTES + B_BYTES;             // 32 or 48 KB
+  static constexpr int STAGES = (192 * 1024) / STAGE;         // 6 or 4
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+  static_assert(SMEM <= 227 * 1024, "dynamic shared memory above the opt-in limit");
+};
+
+template <bool FP8, int NB>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     xf_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kblocks,
                   int64_t total_iters, float* __restrict__ partials, int max_segs, unsigned* err) {
+  using C = Tc2Cfg<NB>;
+  constexpr int TC2_BN = C::BN, TC2_A_BYTES = C::A_BYTES, TC2_STAGE = C::STAGE, TC2_STAGES = C::STAGES;
   constexpr int KELEMS = FP8 ? 128 : 64;  // elements of K per k block
   constexpr int KSTEPS = TC_ROW_BYTES / 32;
   constexpr uint32_t IDESC = make_idesc<FP8>(2 * TC_BM, 256);
@@ -393,7 +366,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   }
   if (warp == 1) {  // both CTAs take part in the pair's allocation
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(512)
+                 "r"(TC2_BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
@@ -422,7 +395,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         uint8_t* sB = sA + TC2_A_BYTES;
         tma_load_2d_pair(sA, &tmA, kb * KELEMS, (int)(tile * 2 * TC_BM + rank * TC_BM), bar_cl);
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < NB; ++j)
           tma_load_2d_pair(sB + j * TC_BM * TC_ROW_BYTES, &tmB, kb * KELEMS, (int)(256 * j + rank * TC_BM), bar_cl);
         issued_mask |= 1u << stage;
         last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
@@ -466,7 +439,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
 #pragma unroll
           for (int ks = 0; ks < KSTEPS; ++ks)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < NB; ++j)
               umma_pair<FP8>(tmem_base + (uint32_t)(j * 256), sw128_desc(a0 + ks * 32),
                              sw128_desc(b0 + j * TC_BM * TC_ROW_BYTES + ks * 32), IDESC,
                              (it > seg_begin || ks > 0) ? 1u : 0u);
@@ -528,7 +501,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   cluster_sync_all();
   tc_fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC2_BN) : "memory");
 }
 
 // Y[r, c] = (sum over the CTAs that covered row tile r / 128 of their partial)
@@ -609,12 +582,12 @@ struct TcPlan {
   int64_t total;
 };
 
-// Row tiles of 256 (two MMA halves sharing each F stage) for the widest
-// products, where F's traffic from L2 would otherwise limit the tensor rate.
-static bool tc_m2(int N) { return N > 128 && N <= 256; }
 
-// 512 columns: CTA pairs on 256-row tiles (G counts pairs).
-static bool tc_pair(int N) { return N > 256; }
+// More than 128 columns: CTA pairs on 256-row tiles (G counts pairs).  At
+// 256 columns the pairs measured 5 % (BF16) and 12 % (E4M3) faster than one
+// CTA on a 256-row tile; at 512 they lift the product from 0.63 to 0.94 of
+// the tensor peak.
+static bool tc_pair(int N) { return N > 128; }
 
 static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM, bool pairs = false) {
   TcPlan p;
@@ -636,7 +609,7 @@ static TcPlan tc_plan(int64_t m, int64_t kdim, bool fp8, int bm = TC_BM, bool pa
 size_t tc_gemm_ws_floats(int64_t m, int64_t kdim, int BN) {
   // largest of the plans a product of this width can use
   const bool pairs = tc_pair(BN);
-  const int bm = (tc_m2(BN) || pairs) ? 2 * TC_BM : TC_BM;
+  const int bm = pairs ? 2 * TC_BM : TC_BM;
   size_t need = 0;
   for (int f = 0; f < 2; ++f) {
     const TcPlan p = tc_plan(m, kdim, f != 0, bm, pairs);
@@ -711,15 +684,17 @@ cudaError_t pack_ft_fp8(const float* F, int64_t n, int ldf, int N, int Npad, voi
   return cudaGetLastError();
 }
 
-template <bool FP8>
+template <bool FP8, int NB>
 static cudaError_t launch_tc2(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
                               unsigned* err, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(xf_tc2_kernel<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+  using C = Tc2Cfg<NB>;
+  cudaError_t e =
+      cudaFuncSetAttribute(xf_tc2_kernel<FP8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * p.G));
   cfg.blockDim = dim3(TC2_THREADS);
-  cfg.dynamicSmemBytes = TC2_SMEM;
+  cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -728,19 +703,19 @@ static cudaError_t launch_tc2(const CUtensorMap& ma, const CUtensorMap& mb, cons
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, xf_tc2_kernel<FP8>, ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  e = cudaLaunchKernelEx(&cfg, xf_tc2_kernel<FP8, NB>, ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
   count_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int BN, bool FP8, bool M2 = false>
+template <int BN, bool FP8>
 static cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcPlan& p, float* ws,
                              unsigned* err, cudaStream_t st) {
-  using C = TcCfg<BN, M2>;
-  cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8, M2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = TcCfg<BN>;
+  cudaError_t e = cudaFuncSetAttribute(xf_tc_kernel<BN, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        C::SMEM);
   if (e != cudaSuccess) return e;
-  xf_tc_kernel<BN, FP8, M2><<<p.G, XF_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
+  xf_tc_kernel<BN, FP8><<<p.G, XF_THREADS, C::SMEM, st>>>(ma, mb, p.kblocks, p.total, ws, p.max_segs, err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -764,8 +739,8 @@ cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, c
   // TMA: 16-byte aligned bases and row pitches
   if (((uintptr_t)X & 15) || ((uintptr_t)Fpack & 15) || (ldx * es) % 16 || (ldp * es) % 16)
     return cudaErrorInvalidValue;
-  const bool m2 = tc_m2(N), pairs = tc_pair(N);
-  const TcPlan p = tc_plan(m, n, fp8, (m2 || pairs) ? 2 * TC_BM : TC_BM, pairs);
+  const bool pairs = tc_pair(N);
+  const TcPlan p = tc_plan(m, n, fp8, pairs ? 2 * TC_BM : TC_BM, pairs);
   if (ws_floats < (size_t)p.G * p.max_segs * p.bm * BN) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   const uint32_t kel = fp8 ? 128 : 64;
@@ -781,16 +756,16 @@ cudaError_t tc_gemm(int fmt, const void* X, int64_t ldx, int64_t m, int64_t n, c
       case 32: e = launch_tc<32, true>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, true>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, true>(ma, mb, p, ws, err, st); break;
-      case 256: e = launch_tc<256, true, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc2<true>(ma, mb, p, ws, err, st); break;
+      case 256: e = launch_tc2<true, 1>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc2<true, 2>(ma, mb, p, ws, err, st); break;
     }
   } else {
     switch (BN) {
       case 32: e = launch_tc<32, false>(ma, mb, p, ws, err, st); break;
       case 64: e = launch_tc<64, false>(ma, mb, p, ws, err, st); break;
       case 128: e = launch_tc<128, false>(ma, mb, p, ws, err, st); break;
-      case 256: e = launch_tc<256, false, true>(ma, mb, p, ws, err, st); break;
-      default: e = launch_tc2<false>(ma, mb, p, ws, err, st); break;
+      case 256: e = launch_tc2<false, 1>(ma, mb, p, ws, err, st); break;
+      default: e = launch_tc2<false, 2>(ma, mb, p, ws, err, st); break;
     }
   }
   if (ev_end) cudaEventRecord(ev_end, st);
