@@ -354,10 +354,10 @@ __device__ __forceinline__ void gb_df_add(float& hi, float& lo, float h2, float 
 
 // The row work of one thread for a problem of width k <= KMAX (G rows padded to KMAX).
 template <int KMAX>
-__device__ __forceinline__ void grouped_hals_row(const HalsProb& P, int g, long long row, float* Fu_all,
-                                                 const float* Ff_all, const float* Y_all, const float* Gs,
-                                                 const float* inv, float alpha, unsigned* err, float2& trv,
-                                                 float2& ddv) {
+__device__ __forceinline__ void grouped_hals_row(const HalsProb& P, int g, long long row, float* __restrict__ Fu_all,
+                                                 const float* __restrict__ Ff_all, const float* __restrict__ Y_all,
+                                                 const float* Gs, const float* inv, float alpha, unsigned* err,
+                                                 float2& trv, float2& ddv) {
   const int k = P.k, RW = P.R * k;
   const long long o = P.f_off + row * RW + (long long)g * k;
   // z = Y + alpha F_fix (as the row routine forms it), so that only w and z
@@ -387,6 +387,31 @@ __device__ __forceinline__ void grouped_hals_row(const HalsProb& P, int g, long 
                          [](int) { return 0.f; }, [](int, float) {});
   bool bad = false;
   float t0 = 0.f, t1 = 0.f, d0 = 0.f, d1 = 0.f;
+  if ((k & 3) == 0 && (o & 3) == 0) {  // 16-byte row segments
+#pragma unroll
+    for (int q = 0; q < KMAX / 4; ++q)
+      if (4 * q < k) {
+        const float4 y = *reinterpret_cast<const float4*>(Y_all + o + 4 * q);
+        const float4 h = *reinterpret_cast<const float4*>(Ff_all + o + 4 * q);
+        const float4 wq = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        *reinterpret_cast<float4*>(Fu_all + o + 4 * q) = wq;
+        if (!isfinite(wq.x) || !isfinite(wq.y) || !isfinite(wq.z) || !isfinite(wq.w)) bad = true;
+        t0 = fmaf(wq.x, y.x, t0);
+        t1 = fmaf(wq.y, y.y, t1);
+        t0 = fmaf(wq.z, y.z, t0);
+        t1 = fmaf(wq.w, y.w, t1);
+        const float4 d = make_float4(wq.x - h.x, wq.y - h.y, wq.z - h.z, wq.w - h.w);
+        d0 = fmaf(d.x, d.x, d0);
+        d1 = fmaf(d.y, d.y, d1);
+        d0 = fmaf(d.z, d.z, d0);
+        d1 = fmaf(d.w, d.w, d1);
+      }
+    if (bad) set_error(err, ERR_NAN);
+    trv.x = t0 + t1;
+    ddv.x = d0 + d1;
+    return;
+  }
+  // Y and F_fix again (cache hits; restrict pointers let the loads run ahead of the stores)
 #pragma unroll
   for (int j = 0; j < KMAX; ++j)
     if (j < k) {
