@@ -559,11 +559,20 @@ __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb
   for (int t = 0; t < 2; ++t)
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[t][e] = make_float2(0.f, 0.f);
+  // rows staged compactly (pitch RW); 16-byte copies and loads when the widths allow
+  const bool vec = (RW & 3) == 0 && (P.f_off & 3) == 0 && (k & 3) == 0;
   for (long long rb = r0; rb < r1; rb += GG_SUB) {
     const int rows = (int)min((long long)GG_SUB, r1 - rb);
-    for (int e = tid; e < GG_SUB * RW; e += GG_THREADS) {
-      const int rr = e / RW, c = e - rr * RW;
-      Fs[rr * GB_BN + c] = rr < rows ? F[(rb + rr) * RW + c] : 0.f;
+    if (vec) {
+      const int nv = rows * RW / 4, nz = GG_SUB * RW / 4;
+      const float4* src = reinterpret_cast<const float4*>(F + rb * RW);
+      float4* dst = reinterpret_cast<float4*>(Fs);
+      for (int e = tid; e < nz; e += GG_THREADS) dst[e] = e < nv ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int e = tid; e < GG_SUB * RW; e += GG_THREADS) {
+        const int rr = e / RW;
+        Fs[e] = rr < rows ? F[rb * RW + e] : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -577,12 +586,19 @@ __global__ void __launch_bounds__(GG_THREADS) grouped_gram_kernel(const HalsProb
 #pragma unroll
         for (int e = 0; e < 16; ++e) f[e] = 0.f;
         for (int rr = rg; rr < GG_SUB; rr += RG) {
-          const float* row = Fs + rr * GB_BN + g * k;
+          const float* row = Fs + rr * RW + g * k;
           float av[4], bv[4];
+          if (vec) {
+            const float4 a4 = *reinterpret_cast<const float4*>(row + ti * 4);
+            const float4 b4 = *reinterpret_cast<const float4*>(row + tj * 4);
+            av[0] = a4.x, av[1] = a4.y, av[2] = a4.z, av[3] = a4.w;
+            bv[0] = b4.x, bv[1] = b4.y, bv[2] = b4.z, bv[3] = b4.w;
+          } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            av[q] = (ti * 4 + q < k) ? row[ti * 4 + q] : 0.f;
-            bv[q] = (tj * 4 + q < k) ? row[tj * 4 + q] : 0.f;
+            for (int q = 0; q < 4; ++q) {
+              av[q] = (ti * 4 + q < k) ? row[ti * 4 + q] : 0.f;
+              bv[q] = (tj * 4 + q < k) ? row[tj * 4 + q] : 0.f;
+            }
           }
 #pragma unroll
           for (int a = 0; a < 4; ++a)
