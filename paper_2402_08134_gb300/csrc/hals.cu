@@ -10,15 +10,14 @@
 namespace symnmf {
 
 constexpr int HALS_THREADS = 128;
+// Column stride (floats) of the staged row tiles: one past the block's rows,
+// so that a thread's walk down its own column and the warp's transposing
+// stores both spread over the banks.
+constexpr int HALS_CS = HALS_THREADS + 1;
 
-// Threads per row of the full-X HALS kernel.  A split over a lane pair (half
-// the registers, twice the warps) measured slower at k = 64 (766 vs 664 us at
-// n = 10^6): the shuffle joins every column's dependency chain, which is bound
-// by shared-memory load latency already.
-template <int KMAX>
-constexpr int hals_ns() {
-  return 1;
-}
+// One thread per row.  A split of each row over a lane pair (half the
+// registers, twice the warps) measured slower at k = 64 (766 vs 664 us at
+// n = 10^6): the shuffle joins every column's dependency chain.
 
 // Widths at which the column loop runs rolled, in rotating blocks of 16
 // (hals_row_rotating): the fully unrolled 64-column body misses the
@@ -28,36 +27,95 @@ constexpr bool hals_rot() {
   return KMAX >= 48;
 }
 
+template <int KMAX>
+constexpr int hals_gstride() {
+  return hals_rot<KMAX>() ? 2 * KMAX : KMAX;
+}
+
+// Copy the warp's 32 rows [r0, r0 + 32) of a row-major matrix (row stride ld,
+// k columns) into the column-major tile T (column c of tile row t at
+// T[c HALS_CS + t], tile rows wrow .. wrow + 31), zero padded past n and k.
+// The lanes walk the rows' contiguous span, so each global load instruction
+// covers whole cache lines (one row per thread would touch 32 lines per load).
+template <int KMAX, bool VEC>
+__device__ __forceinline__ void hals_stage_in(const float* __restrict__ src, int64_t ld, int64_t r0, int64_t n,
+                                              int k, float* T, int wrow, int lane) {
+  if constexpr (VEC) {
+    constexpr int Q = KMAX / 4;
+#pragma unroll 4
+    for (int e = lane; e < 32 * Q; e += 32) {
+      const int rr = e / Q, c4 = e - rr * Q;
+      const int64_t r = r0 + rr;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < n && 4 * c4 < k) v = __ldg(reinterpret_cast<const float4*>(src + r * ld) + c4);
+      float* t = T + 4 * c4 * HALS_CS + wrow + rr;
+      t[0] = v.x, t[HALS_CS] = v.y, t[2 * HALS_CS] = v.z, t[3 * HALS_CS] = v.w;
+    }
+  } else {
+#pragma unroll 4
+    for (int e = lane; e < 32 * KMAX; e += 32) {
+      const int rr = e / KMAX, c = e - rr * KMAX;
+      const int64_t r = r0 + rr;
+      T[c * HALS_CS + wrow + rr] = (r < n && c < k) ? __ldg(src + r * ld + c) : 0.f;
+    }
+  }
+}
+
+// The inverse of hals_stage_in: rows r0 .. min(r0 + 32, n) - 1 of the
+// row-major dst (row stride k) from the tile, columns < k only.
+template <int KMAX, bool VEC>
+__device__ __forceinline__ void hals_stage_out(float* __restrict__ dst, int64_t r0, int64_t n, int k,
+                                               const float* T, int wrow, int lane) {
+  if constexpr (VEC) {
+    constexpr int Q = KMAX / 4;
+#pragma unroll 4
+    for (int e = lane; e < 32 * Q; e += 32) {
+      const int rr = e / Q, c4 = e - rr * Q;
+      const int64_t r = r0 + rr;
+      const float* t = T + 4 * c4 * HALS_CS + wrow + rr;
+      if (r < n && 4 * c4 < k)
+        reinterpret_cast<float4*>(dst + r * k)[c4] = make_float4(t[0], t[HALS_CS], t[2 * HALS_CS], t[3 * HALS_CS]);
+    }
+  } else {
+#pragma unroll 4
+    for (int e = lane; e < 32 * KMAX; e += 32) {
+      const int rr = e / KMAX, c = e - rr * KMAX;
+      const int64_t r = r0 + rr;
+      if (r < n && c < k) dst[r * k + c] = T[c * HALS_CS + wrow + rr];
+    }
+  }
+}
+
 // Full-X HALS update, Eq. symhals_update2:
 //   w_i <- max(0, (Y_i + alpha h_i - sum_{j != i} w_j G_ji) / (G_ii + alpha)),
-// i = 0..k-1 in order with the columns already updated.  NS = hals_ns threads
-// per row, each holding its KMAX / NS columns of F_upd in registers and of Y
-// in its own column of shared memory (zero padded; 16-byte loads when VEC).
+// i = 0..k-1 in order with the columns already updated.  One thread per row:
+// the row of F_upd in registers, its rows of Y and F_fix in the thread's own
+// columns of two shared-memory tiles (zero padded).  Each warp moves its 32
+// rows between global and shared memory itself, with whole-line loads and
+// stores (hals_stage_in / hals_stage_out), so only warp barriers are needed.
 // G with its diagonal zeroed and the reciprocals 1 / (G_ii + alpha) sit in
 // shared memory, read as broadcasts.  With U given, the row of Y is formed as
 // U_r M (LAI, M = Lambda U^T F_fix in shared memory).  Persistent grid over
-// rows; F_upd . Y and ||F_upd - F_fix||^2 are kept per thread in double-float
-// and reduced in FP64.
+// 128-row tiles; F_upd . Y and ||F_upd - F_fix||^2 are kept per thread in
+// double-float and reduced in FP64.
 template <int KMAX, bool VEC>
 __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
     float* __restrict__ Fu, const float* __restrict__ Ff, int64_t n, int k, const float* __restrict__ G, float alpha,
     const float* __restrict__ Y, int ldy, const float* __restrict__ U, int l, const float* __restrict__ M,
     double* part, double* ws, unsigned* counter, unsigned* err) {
-  constexpr int NS = hals_ns<KMAX>(), KH = KMAX / NS;
   constexpr bool ROT = hals_rot<KMAX>();
-  constexpr int RS = ROT ? 2 * KMAX : hals_split_stride<KMAX, NS>();
-  constexpr int RPB = HALS_THREADS / NS;  // rows per block and pass
+  constexpr int RS = hals_gstride<KMAX>();
   extern __shared__ __align__(16) float sm[];
-  float* Gs = sm;               // KMAX x RS, diagonal zeroed
-  float* inv = Gs + KMAX * RS;  // KMAX
-  float* Ys = inv + KMAX;       // KH x HALS_THREADS: each thread's row of Y, column-major
-  float* Ms = Ys + KH * HALS_THREADS;  // l x KMAX (LAI only)
-  const int tid = threadIdx.x;
+  float* Gs = sm;                  // KMAX x RS, diagonal zeroed (rows twice side by side when ROT)
+  float* inv = Gs + KMAX * RS;     // KMAX
+  float* Ta = inv + KMAX;          // KMAX x HALS_CS: rows of F_upd, then of Y, then of F_upd again
+  float* Tb = Ta + KMAX * HALS_CS;  // KMAX x HALS_CS: rows of F_fix
+  float* Ms = Tb + KMAX * HALS_CS;  // l x KMAX (LAI only); 16-byte aligned as KMAX % 4 == 0
+  const int tid = threadIdx.x, lane = tid & 31, wrow = tid & ~31;
   for (int e = tid; e < KMAX * KMAX; e += HALS_THREADS) {
     const int i = e / KMAX, j = e - i * KMAX;
-    const int part = j / KH;
     const float v = (i < k && j < k && i != j) ? G[i * k + j] : 0.f;
-    Gs[i * RS + part * (NS > 1 ? KH + 4 : KH) + (j - part * KH)] = v;
+    Gs[i * RS + j] = v;
     if constexpr (ROT) Gs[i * RS + KMAX + j] = v;  // each row twice (rotated reads)
   }
   if (U)
@@ -68,82 +126,63 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
   if (tid < KMAX) inv[tid] = tid < k ? 1.0f / (G[tid * k + tid] + alpha) : 0.f;
   __syncthreads();
 
-  const int p = NS > 1 ? (tid & 1) : 0;            // this thread's part of its row
-  const unsigned mask = NS > 1 ? 3u << (tid & 30) : 0xffffffffu;
-  const int c0 = p * KH;                             // its first column
-  const float4* Gp4 = reinterpret_cast<const float4*>(Gs + p * (KH + 4));
-  const float4* Ms4 = reinterpret_cast<const float4*>(Ms + c0);
+  const float4* G4 = reinterpret_cast<const float4*>(Gs);
+  const float4* Ms4 = reinterpret_cast<const float4*>(Ms);
   float2 trv = make_float2(0.f, 0.f), ddv = make_float2(0.f, 0.f);
   bool bad = false;
-  float* ys = Ys + tid;  // this thread's column: y_c at ys[c * HALS_THREADS] (no bank conflicts)
-  for (int64_t r = (int64_t)blockIdx.x * RPB + tid / NS; r < n; r += (int64_t)gridDim.x * RPB) {
-    float w[KH];
-    float* fu = Fu + r * k + c0;
-    const float* fx = Ff + r * k + c0;
-    if constexpr (VEC) {
+  float* ya = Ta + tid;  // this thread's columns: entry c at [c HALS_CS]
+  const float* fb = Tb + tid;
+  // uniform trip count over the block: rows past n run on zeros and are not stored
+  for (int64_t t0 = (int64_t)blockIdx.x * HALS_THREADS; t0 < n; t0 += (int64_t)gridDim.x * HALS_THREADS) {
+    const int64_t r0 = t0 + wrow;  // this warp's first row
+    float w[KMAX];
+    __syncwarp();  // the previous tile's stores have read Ta
+    hals_stage_in<KMAX, VEC>(Fu, k, r0, n, k, Ta, wrow, lane);
+    __syncwarp();
 #pragma unroll
-      for (int q = 0; q < KH / 4; ++q) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + 4 * q < k) v = __ldg(reinterpret_cast<const float4*>(fu) + q);
-        w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < KH; ++c) w[c] = c0 + c < k ? __ldg(fu + c) : 0.f;
-    }
-    // this row of Y into shared memory (read once per column there: fewer registers)
+    for (int c = 0; c < KMAX; ++c) w[c] = ya[c * HALS_CS];
+    __syncwarp();  // all lanes hold their rows before Ta takes Y
     if (U) {  // Y_r = U_r M (LAI product fused into the update)
-      float y[KH];
+      const int64_t r = r0 + lane;
+      float y[KMAX];
 #pragma unroll
-      for (int c = 0; c < KH; ++c) y[c] = 0.f;
-      const float* ur = U + r * l;
+      for (int c = 0; c < KMAX; ++c) y[c] = 0.f;
+      if (r < n) {
+        const float* ur = U + r * l;
 #pragma unroll 2
-      for (int pp = 0; pp < l; ++pp) {
-        const float u = __ldg(ur + pp);
+        for (int pp = 0; pp < l; ++pp) {
+          const float u = __ldg(ur + pp);
 #pragma unroll
-        for (int q = 0; q < KH / 4; ++q) {
-          const float4 m = Ms4[pp * (KMAX / 4) + q];
-          y[4 * q + 0] = fmaf(u, m.x, y[4 * q + 0]);
-          y[4 * q + 1] = fmaf(u, m.y, y[4 * q + 1]);
-          y[4 * q + 2] = fmaf(u, m.z, y[4 * q + 2]);
-          y[4 * q + 3] = fmaf(u, m.w, y[4 * q + 3]);
+          for (int q = 0; q < KMAX / 4; ++q) {
+            const float4 m = Ms4[pp * (KMAX / 4) + q];
+            y[4 * q + 0] = fmaf(u, m.x, y[4 * q + 0]);
+            y[4 * q + 1] = fmaf(u, m.y, y[4 * q + 1]);
+            y[4 * q + 2] = fmaf(u, m.z, y[4 * q + 2]);
+            y[4 * q + 3] = fmaf(u, m.w, y[4 * q + 3]);
+          }
         }
       }
 #pragma unroll
-      for (int c = 0; c < KH; ++c) ys[c * HALS_THREADS] = y[c];
-    } else if constexpr (VEC) {
-      const float* yr = Y + r * ldy + c0;
-#pragma unroll
-      for (int q = 0; q < KH / 4; ++q) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + 4 * q < k) v = __ldg(reinterpret_cast<const float4*>(yr) + q);
-        ys[(4 * q) * HALS_THREADS] = v.x, ys[(4 * q + 1) * HALS_THREADS] = v.y;
-        ys[(4 * q + 2) * HALS_THREADS] = v.z, ys[(4 * q + 3) * HALS_THREADS] = v.w;
-      }
+      for (int c = 0; c < KMAX; ++c) ya[c * HALS_CS] = y[c];
     } else {
-#pragma unroll
-      for (int c = 0; c < KH; ++c) ys[c * HALS_THREADS] = c0 + c < k ? __ldg(Y + r * ldy + c0 + c) : 0.f;
+      hals_stage_in<KMAX, VEC>(Y, ldy, r0, n, k, Ta, wrow, lane);
     }
-    // the fixed row is read column by column (L1 hits after the first); the
-    // shared-memory column of Y is this thread's own, so no barrier is needed
+    hals_stage_in<KMAX, VEC>(Ff, k, r0, n, k, Tb, wrow, lane);
+    __syncwarp();
     if constexpr (ROT)
       bad |= hals_row_rotating<KMAX, 16>(
-          w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, Gs, inv, [&](int c) { return __ldg(fx + c); },
+          w, [&](int c) { return ya[c * HALS_CS]; }, alpha, k, Gs, inv, [&](int c) { return fb[c * HALS_CS]; },
           trv, ddv);
     else
-      bad |= hals_row_split<KMAX, NS>(
-          w, [&](int c) { return ys[c * HALS_THREADS]; }, alpha, k, p, mask, Gp4, inv,
-          [&](int c) { return __ldg(fx + c); }, trv, ddv);
-    if constexpr (VEC) {
+      bad |= hals_row_split<KMAX, 1>(
+          w, [&](int c) { return ya[c * HALS_CS]; }, alpha, k, 0, 0xffffffffu, G4, inv,
+          [&](int c) { return fb[c * HALS_CS]; }, trv, ddv);
+    // the row back into this thread's columns of Ta (only its own reads of Y
+    // were there), then the warp's whole-line stores
 #pragma unroll
-      for (int q = 0; q < KH / 4; ++q)
-        if (c0 + 4 * q < k)
-          reinterpret_cast<float4*>(fu)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-    } else {
-#pragma unroll
-      for (int c = 0; c < KH; ++c)
-        if (c0 + c < k) fu[c] = w[c];
-    }
+    for (int c = 0; c < KMAX; ++c) ya[c * HALS_CS] = w[c];
+    __syncwarp();
+    hals_stage_out<KMAX, VEC>(Fu, r0, n, k, Ta, wrow, lane);
   }
   if (bad) set_error(err, ERR_NAN);
   __shared__ double sh[32];
@@ -163,8 +202,7 @@ template <int KMAX, bool VEC>
 static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, const float* G, double alpha,
                                const float* Y, int ldy, const float* U, int l, const float* M, double* part,
                                double* ws, unsigned* counter, unsigned* err, cudaStream_t st) {
-  const int rs = hals_rot<KMAX>() ? 2 * KMAX : hals_split_stride<KMAX, hals_ns<KMAX>()>();
-  size_t smem = (size_t)(KMAX * rs + KMAX + (KMAX / hals_ns<KMAX>()) * HALS_THREADS) * 4;
+  size_t smem = (size_t)(KMAX * hals_gstride<KMAX>() + KMAX + 2 * KMAX * HALS_CS) * 4;
   if (U) smem += (size_t)l * KMAX * 4;
   auto kern = hals_kernel<KMAX, VEC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -172,8 +210,7 @@ static cudaError_t launch_hals(float* Fu, const float* Ff, int64_t n, int k, con
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HALS_THREADS, smem);
   if (e != cudaSuccess) return e;
-  const int64_t rpb = HALS_THREADS / hals_ns<KMAX>();
-  const int64_t tiles = (n + rpb - 1) / rpb;
+  const int64_t tiles = (n + HALS_THREADS - 1) / HALS_THREADS;
   // at most 2048 blocks: one FP64 partial pair per block in ws
   int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * std::min(std::max(per_sm, 1), 8));
   grid = std::max(1, std::min(grid, 2048));

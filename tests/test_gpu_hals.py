@@ -123,8 +123,8 @@ def test_rejects_bad_inputs(S):
 
 
 def test_edge_sizes(S):
-    # n = 1 and k = 1 and a ragged n that spans several tiles
-    for n, k in [(1, 1), (5, 3), (129, 1), (1031, 64)]:
+    # n = 1 and k = 1 and ragged n that span several 128-row tiles, with and without 16-byte rows
+    for n, k in [(1, 1), (5, 3), (129, 1), (1031, 64), (300, 50), (2053, 20), (161, 48)]:
         rng = np.random.default_rng(n)
         A = rng.random((n, n))
         X = 0.5 * (A + A.T)
