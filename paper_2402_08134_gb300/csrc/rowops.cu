@@ -214,8 +214,18 @@ size_t xcross_ws_doubles(int la, int lb) { return (size_t)XC_MAX_BLOCKS_PER_SM *
 // terms of size ||X||^2, so the Grams need this accuracy.  Block partials are
 // summed in block order (deterministic), by the last block or by a second
 // kernel.  VEC: 16-byte loads of whole rows (la, lb, lda, ldb multiples of 4,
-// aligned operands).
+// aligned operands).  A Gram of rows without weights, VEC and at most
+// XC_PIPE_MAX columns, stages its row chunks with asynchronous 16-byte copies
+// into two buffers, the next chunk in flight while the current one is summed.
 constexpr int XC_SUB = 32;
+constexpr int XC_PIPE_MAX = 64;
+
+__device__ __forceinline__ void xc_cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void xc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void xc_cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Tile index -> (row tile, column tile): row-major over all ta x tb tiles, or
 // over the upper triangle (ti <= tj) of a symmetric product.
@@ -256,8 +266,10 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
   float* As = (float*)smraw;
   // a Gram (same operand, no weights) stages its rows once
   const bool same = (A == B) && (lda == ldb) && (la == lb) && !wt;
-  float* Bs = As + XC_CHUNK * la4;
-  dfl* red = (dfl*)(Bs + (same ? 0 : XC_CHUNK * lb4));
+  const bool pipe = VEC && same && la4 <= XC_PIPE_MAX;
+  float* Bs = As + XC_CHUNK * la4;  // the second buffer of As when pipe
+  // the row-group sums reuse the staging buffers after the last chunk
+  dfl* red = (dfl*)smraw;
   dfl* wsd = reinterpret_cast<dfl*>(ws);  // the partials are double-float pairs
   // a symmetric product (same operand on both sides, weights allowed) covers
   // the upper tiles only and mirrors them: exactly symmetric, half the work
@@ -291,10 +303,35 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
     xc_tile(tile < T ? tile : 0, sym, ta, tb, tile_i[t], tile_j[t]);
     if (tile >= T || !active) tile_i[t] = -1;  // idle threads own no tile
   }
-  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK) {
-    // stage the chunk (rows past the end and pad columns are zero)
+  // chunk [rb, rb + XC_CHUNK) of the Gram rows into dst by asynchronous copies
+  // (rows past the end are zero), as one commit group
+  auto stage_async = [&](int64_t rb, float* dst) {
+    if (rb < r1 && a_r < a_rpp) {
+      const int rows = (int)min((int64_t)XC_CHUNK, r1 - rb);
+      for (int rr = a_r; rr < XC_CHUNK; rr += a_rpp) {
+        float* d = dst + rr * la4 + 4 * a_c;
+        if (rr < rows) {
+          const int64_t src = idx ? (int64_t)__ldg(idx + rb + rr) : rb + rr;
+          xc_cp_async16(d, A + src * lda + 4 * a_c);
+        } else {
+          *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    }
+    xc_cp_commit();
+  };
+  if (pipe) stage_async(r0, As);
+  int it = 0;
+  for (int64_t rb = r0; rb < r1; rb += XC_CHUNK, ++it) {
     const int rows = (int)min((int64_t)XC_CHUNK, r1 - rb);
-    if (a_r < a_rpp) {
+    const float* Acur = As;
+    if (pipe) {
+      // the other buffer was last read before the previous chunk's closing barrier
+      Acur = (it & 1) ? Bs : As;
+      stage_async(rb + XC_CHUNK, (it & 1) ? As : Bs);
+      xc_cp_wait_prev();  // this chunk's copies (all groups but the newest) have landed
+    } else if (a_r < a_rpp) {
+      // stage the chunk (rows past the end and pad columns are zero)
 #pragma unroll 4
       for (int rr = a_r; rr < XC_CHUNK; rr += a_rpp) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -343,8 +380,8 @@ __global__ void __launch_bounds__(XC_THREADS) xcross_kernel(
 #pragma unroll
       for (int t = 0; t < TPT; ++t) {
         if (tile_i[t] >= 0) {
-          const float* ap = As + 4 * tile_i[t];
-          const float* bp = Bsrc + 4 * tile_j[t];
+          const float* ap = Acur + 4 * tile_i[t];
+          const float* bp = (same ? Acur : Bsrc) + 4 * tile_j[t];
           for (int s0 = rg; s0 < rows; s0 += XC_SUB * R) {
             const int s1 = min(rows, s0 + XC_SUB * R);
             float p[16];
@@ -472,11 +509,13 @@ cudaError_t xcross(const float* A, int lda, int la, const float* B, int ldb, int
   // as many threads as tiles x row groups use (whole warps): narrow products
   // leave room for more blocks per SM
   const int nthreads = T >= XC_THREADS ? XC_THREADS : ((XC_THREADS / T) * T + 31) / 32 * 32;
-  const size_t smem =
-      (size_t)XC_CHUNK * (la4 + (same ? 0 : lb4)) * 4 + (size_t)(T < XC_THREADS ? T : 0) * 16 * 8;
   const int tpt = T <= XC_THREADS ? 1 : T <= 2 * XC_THREADS ? 2 : 4;
   const bool vec = (la % 4) == 0 && (lb % 4) == 0 && (lda % 4) == 0 && (ldb % 4) == 0 &&
                    (((uintptr_t)A | (uintptr_t)B) & 15) == 0;
+  const bool pipe = vec && same && la4 <= XC_PIPE_MAX;  // two buffers of A rows
+  // the row-group sums reuse the staging space after the last chunk
+  const size_t smem = std::max((size_t)XC_CHUNK * (la4 + (same ? (pipe ? la4 : 0) : lb4)) * 4,
+                               (size_t)(T < XC_THREADS ? T : 0) * 16 * 8);
   const void* fn = tpt == 1 ? (vec ? (const void*)xcross_kernel<1, true> : (const void*)xcross_kernel<1, false>)
                    : tpt == 2 ? (vec ? (const void*)xcross_kernel<2, true> : (const void*)xcross_kernel<2, false>)
                               : (vec ? (const void*)xcross_kernel<4, true> : (const void*)xcross_kernel<4, false>);

@@ -25,9 +25,10 @@ def _solver(S, dev, n, k, **kw):
     return S.Solver(csr=(dev["row_ptr"], dev["col"], dev["val"]), k=k, n=n, **kw)
 
 
-def test_leverage_scores(S):
-    n, k = 20000, 16
-    _, Xs, dev = _sbm(n, 16, k, seed=0)
+@pytest.mark.parametrize("n,k", [(20000, 16), (1031, 64), (777, 50), (300, 5), (3, 2)])
+def test_leverage_scores(S, n, k):
+    # ragged n against the 256-row tiles of the row pass, 16-byte rows (k % 4 == 0) and not
+    _, Xs, dev = _sbm(n, 16 if n >= 1000 else 1, k, seed=0, deg=min(30.0, n / 8))
     s = _solver(S, dev, n, k, seed=3)
     Hi = uniform_factor(n, k, seed=1)
     s.set_factors(t32(Hi))
