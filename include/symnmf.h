@@ -292,6 +292,25 @@ symnmf_status symnmf_lvs_iterate(symnmf_t h, int iter0, int iters, double tau, i
 symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double* surrogate_obj,
                               double* proj_grad);
 
+/* Sweeps of `source` (rule HALS) in chunks of `chunk`, each chunk followed by
+ * the normalized residual ||X - W H^T||_F / ||X||_F of the operator `check`
+ * (as symnmf_residual computes it); stops after the first check at or below
+ * `target`, or after max_sweeps sweeps.  The residual-check schedule of the
+ * experiments (a check every few iterations, stop once the residual is
+ * reached), with the decision taken on the device: for SRC_LAI sweeps of the
+ * persistent engine with max_sweeps a multiple of chunk, once a call repeats
+ * the previous call's check, chunk, max_sweeps / chunk, target and sketch
+ * width, the first chunk and check run eagerly and the rest in one CUDA graph
+ * (recorded on that call, replayed by later ones) whose WHILE node repeats
+ * chunk, check and decision until the decision stops it, so no host round
+ * trip separates the checks.  Otherwise the host checks after each chunk.
+ * Both give the same results to the last bit.  Outputs (host, each may be
+ * NULL): the sweeps run, the checks made (at most LOOP_MAX = 1024, else
+ * SYMNMF_EINVAL) and the last check's residual.  Synchronises once at the end
+ * (device loop) or once per chunk. */
+symnmf_status symnmf_sweep_to_target(symnmf_t h, int source, int check, int chunk, int max_sweeps, double target,
+                                     int* sweeps_out, int* checks_out, double* nr_out);
+
 /* -------------------------------------------------- standalone kernels */
 
 /* Y = X F for a dense X (fmt F64/F32/BF16/FP8, ld ldx, FP8 with row_scale),

@@ -98,6 +98,7 @@ _SIGS = {
     "symnmf_lvs_update": (_I, [_P, _I, _I]),
     "symnmf_lvs_iterate": (_I, [_P, _I, _I, _D, _I, _I]),
     "symnmf_residual": (_I, [_P, _I, _DP, _DP, _DP]),
+    "symnmf_sweep_to_target": (_I, [_P, _I, _I, _I, _I, _D, C.POINTER(_I), C.POINTER(_I), _DP]),
     "symnmf_dense_xf": (_I, [_I, _P, _I64, _P, _I64, _P, _I, _I, _P, _I, _I, _P]),
     "symnmf_csr_xf": (_I, [_P, _P, _P, _I64, _P, _I, _P, _P]),
     "symnmf_gram": (_I, [_P, _I64, _I, _P, _P]),
@@ -386,6 +387,14 @@ class Solver:
         nr, ob, pg = C.c_double(), C.c_double(), C.c_double()
         self._chk(symnmf_residual(self.h, source, C.byref(nr), C.byref(ob), C.byref(pg) if proj_grad else None))
         return (nr.value, ob.value, pg.value) if proj_grad else (nr.value, ob.value)
+
+    def sweep_to_target(self, target, *, source=SRC_LAI, check=SRC_X, chunk=10, max_sweeps=200):
+        """Sweeps in chunks with a residual check after each, stopping at `target` (symnmf_sweep_to_target).
+        Returns dict(sweeps, checks, nr) with the last check's normalized residual."""
+        sw, ch, nr = _I(), _I(), C.c_double()
+        self._chk(symnmf_sweep_to_target(self.h, source, check, int(chunk), int(max_sweeps), float(target),
+                                         C.byref(sw), C.byref(ch), C.byref(nr)))
+        return {"sweeps": sw.value, "checks": ch.value, "nr": nr.value}
 
 
 class Batch:

@@ -430,6 +430,7 @@ extern "C" void symnmf_destroy(symnmf_t h) {
   if (!h) return;
   for (auto& g : h->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->loop.exec) cudaGraphExecDestroy(h->loop.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (auto& pr : h->prof_events) {
     cudaEventDestroy(pr.first);
@@ -762,6 +763,17 @@ static symnmf_status get_graph(symnmf_t h, int src, int rule, symnmf_ctx::Graph*
   return SYMNMF_OK;
 }
 
+// The handle's Grams follow the engine's final factors.
+static symnmf_status engine_grams(symnmf_t h) {
+  const int k = h->k;
+  TRY(cudaMemcpyAsync(h->Gd[0], h->eng_G, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+  TRY(cudaMemcpyAsync(h->Gd[1], h->eng_G + k * k, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+  TRY(to_float_scaled(h->Gd[0], k, k, nullptr, h->Gf[0], h->st));
+  TRY(to_float_scaled(h->Gd[1], k, k, nullptr, h->Gf[1], h->st));
+  h->grams_fresh = true;
+  return SYMNMF_OK;
+}
+
 // LAI-HALS sweeps in one cooperative launch per chunk of sweeps.
 static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host) {
   const int k = h->k;
@@ -798,14 +810,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
     }
     done += chunk;
   }
-  if (nsweeps > 0) {
-    // the handle's Grams follow the engine's final factors
-    TRY(cudaMemcpyAsync(h->Gd[0], h->eng_G, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
-    TRY(cudaMemcpyAsync(h->Gd[1], h->eng_G + k * k, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
-    TRY(to_float_scaled(h->Gd[0], k, k, nullptr, h->Gf[0], h->st));
-    TRY(to_float_scaled(h->Gd[1], k, k, nullptr, h->Gf[1], h->st));
-    h->grams_fresh = true;
-  }
+  if (nsweeps > 0) TRYS(engine_grams(h));
   return SYMNMF_OK;
 }
 
@@ -1135,6 +1140,30 @@ extern "C" symnmf_status symnmf_solve(symnmf_t h, const symnmf_schedule* sc, sym
 
 // -------------------------------------------------------------- residual
 
+// Y = X F for the operator `source` (X, its float32 copy, or the LAI).
+static symnmf_status apply_operator(symnmf_t h, int source, const float* F, float* Yo) {
+  const int k = h->k;
+  if (source == SYMNMF_SRC_LAI) {
+    TRY(xcross(h->U, h->l, h->l, F, k, k, h->n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf, h->ws,
+               h->counters + 0, h->st));
+    TRY(apply_small(h->U, h->l, h->l, h->Mf, k, h->n, Yo, k, h->st));
+    return SYMNMF_OK;
+  }
+  return product(h, source, F, k, k, Yo, k);
+}
+
+// The device part of a residual evaluation (Grams current): scal[S_OBJ] =
+// ||X - W H^T||^2 by the trace trick, scal[S_RES + 1] = ||W - H||^2.  No sync.
+static symnmf_status residual_dev(symnmf_t h, int source) {
+  const int k = h->k;
+  TRYS(apply_operator(h, source, h->H, h->Y));  // Y = X H
+  // (sum W .* XH, ||W - H||^2) in one pass
+  TRY(resid_reduce(h->W, h->H, h->Y, h->n * k, h->scal + S_RES, h->ws, h->counters + 6, h->st));
+  TRY(objective(normx_for(h, source), h->Gd[1], h->Gd[0], k, h->scal + S_RES, h->scal + S_ZERO,
+                h->scal + S_OBJ, nullptr, 0, h->st));
+  return SYMNMF_OK;
+}
+
 extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double* surrogate,
                                          double* proj_grad) {
   if (!h) return SYMNMF_EINVAL;
@@ -1143,20 +1172,8 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
   const int k = h->k;
   const int64_t n = h->n;
   if (!h->grams_fresh) TRYS(refresh_grams(h));
-  auto apply_op = [&](const float* F, float* Yo) -> symnmf_status {
-    if (source == SYMNMF_SRC_LAI) {
-      TRY(xcross(h->U, h->l, h->l, F, k, k, n, nullptr, nullptr, nullptr, h->lam, 0.0, nullptr, h->Mf, h->ws,
-                 h->counters + 0, h->st));
-      TRY(apply_small(h->U, h->l, h->l, h->Mf, k, n, Yo, k, h->st));
-      return SYMNMF_OK;
-    }
-    return product(h, source, F, k, k, Yo, k);
-  };
-  TRYS(apply_op(h->H, h->Y));  // Y = X H
-  // (sum W .* XH, ||W - H||^2) in one pass
-  TRY(resid_reduce(h->W, h->H, h->Y, n * k, h->scal + S_RES, h->ws, h->counters + 6, h->st));
-  TRY(objective(normx_for(h, source), h->Gd[1], h->Gd[0], k, h->scal + S_RES, h->scal + S_ZERO,
-                h->scal + S_OBJ, nullptr, 0, h->st));
+  auto apply_op = [&](const float* F, float* Yo) -> symnmf_status { return apply_operator(h, source, F, Yo); };
+  TRYS(residual_dev(h, source));
   double pg2 = 0.0;
   if (proj_grad) {
     TRY(cudaMemsetAsync(h->scal + S_PG, 0, sizeof(double), h->st));
@@ -1175,6 +1192,186 @@ extern "C" symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_re
   if (norm_resid) *norm_resid = sqrt(fmax(r2, 0.0) / nx2);
   if (surrogate) *surrogate = r2 + h->alpha * hs[S_RES + 1];
   if (proj_grad) *proj_grad = sqrt(pg2);
+  return SYMNMF_OK;
+}
+
+// ------------------------------------------------ sweeps to a residual target
+
+// One residual check's decision: NR = sqrt(max(r2, 0) / ||X||^2) into the log,
+// one more check counted, and the loop continues while NR > target and fewer
+// than max_checks checks were made (a NaN NR stops it).  With a handle, the
+// decision also sets the enclosing WHILE node's condition.
+__global__ void loop_decide_kernel(const double* r2, const double* nx2, double target, int max_checks, int* li,
+                                   double* nr_log, cudaGraphConditionalHandle cond, int use_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int c = li[0];
+  const double nr = sqrt(fmax(*r2, 0.0) / *nx2);
+  if (c < LOOP_MAX) nr_log[c] = nr;
+  li[0] = c + 1;
+  const unsigned go = (nr > target && c + 1 < max_checks) ? 1u : 0u;
+  li[1] = (int)go;
+  if (use_cond) cudaGraphSetConditional(cond, go);
+}
+
+// The WHILE node's condition from the first check's decision.
+__global__ void loop_seed_kernel(const int* li, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, li[1] ? 1u : 0u);
+}
+
+// One pass of the loop body: `chunk` LAI sweeps in one engine launch resumed
+// from the previous launch's state, the Grams, the residual of `check`, the
+// decision.
+static symnmf_status loop_body(symnmf_t h, int check, int chunk, double target, int max_checks,
+                               cudaGraphConditionalHandle cond) {
+  TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, h->k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
+                 h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, nullptr, nullptr, true));
+  TRYS(engine_grams(h));
+  TRYS(residual_dev(h, check));
+  loop_decide_kernel<<<1, 32, 0, h->st>>>(h->scal + S_OBJ, normx_for(h, check), target, max_checks, h->loop_i,
+                                          h->loop_nr, cond, 1);
+  count_launches(1);
+  return SYMNMF_OK;
+}
+
+// The loop graph for these parameters: [seed] -> WHILE(cond) { loop_body }.
+// Recorded on the private stream; everything it touches was sized by the
+// eager first pass, so recording allocates nothing.
+static symnmf_status get_loop_graph(symnmf_t h, int check, int chunk, double target, int max_checks) {
+  const void* bufs[5] = {h->U, h->eng_ws, h->fpack, h->gemm_ws, h->loop_i};
+  auto& L = h->loop;
+  if (L.exec && L.check == check && L.chunk == chunk && L.max_checks == max_checks && L.l == h->l &&
+      L.target == target && std::equal(bufs, bufs + 5, L.bufs))
+    return SYMNMF_OK;
+  if (L.exec) {
+    cudaGraphExecDestroy(L.exec);  // one instantiation of a graph with a conditional node at a time
+    L.exec = nullptr;
+  }
+  if (!h->cap_st) TRY(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  TRY(cudaGraphCreate(&g, 0));
+  cudaStream_t saved = h->st;
+  h->st = h->cap_st;
+  uint64_t body_kernels = 0;
+  auto record = [&]() -> symnmf_status {
+    cudaGraphConditionalHandle cond;
+    TRY(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+    TRY(cudaStreamBeginCaptureToGraph(h->st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    loop_seed_kernel<<<1, 32, 0, h->st>>>(h->loop_i, cond);
+    cudaError_t e = cudaGetLastError();
+    cudaGraph_t got = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h->st, &got);
+    TRY(e);
+    TRY(ee);
+    cudaGraphNode_t seed = nullptr;
+    size_t nn = 1;
+    TRY(cudaGraphGetNodes(g, &seed, &nn));
+    if (nn != 1) return fail(h, SYMNMF_ECUDA, "loop graph: expected one seed node");
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    TRY(cudaGraphAddNode(&node, g, &seed, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    TRY(cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    const uint64_t before = g_launches.load();
+    symnmf_status s = loop_body(h, check, chunk, target, max_checks, cond);
+    h->capturing = false;
+    body_kernels = g_launches.load() - before;
+    g_launches -= body_kernels;  // recorded, not launched
+    ee = cudaStreamEndCapture(h->st, &got);
+    if (s != SYMNMF_OK) return s;
+    TRY(ee);
+    TRY(cudaGraphInstantiate(&L.exec, g, 0));
+    return SYMNMF_OK;
+  };
+  symnmf_status s = record();
+  h->st = saved;
+  h->capturing = false;
+  cudaGraphDestroy(g);
+  if (s != SYMNMF_OK) {
+    cudaGetLastError();
+    L.exec = nullptr;
+    return s;
+  }
+  L.check = check;
+  L.chunk = chunk;
+  L.max_checks = max_checks;
+  L.l = h->l;
+  L.target = target;
+  std::copy(bufs, bufs + 5, L.bufs);
+  L.nkernels = body_kernels;
+  return SYMNMF_OK;
+}
+
+extern "C" symnmf_status symnmf_sweep_to_target(symnmf_t h, int source, int check, int chunk, int max_sweeps,
+                                                double target, int* sweeps_out, int* checks_out, double* nr_out) {
+  if (!h || chunk < 1 || max_sweeps < 1 || !(target == target)) return SYMNMF_EINVAL;
+  if (check == SYMNMF_SRC_COMP) return fail(h, SYMNMF_EINVAL, "residual of X, the LAI or the float32 copy");
+  TRYS(validate_sweep(h, source, SYMNMF_RULE_HALS));
+  TRYS(validate_sweep(h, check, SYMNMF_RULE_HALS));
+  const int max_checks = (max_sweeps + chunk - 1) / chunk;
+  if (max_checks > LOOP_MAX) return fail(h, SYMNMF_EINVAL, "more residual checks than the loop records");
+  if (!h->loop_i) {
+    TRY(dalloc(h, &h->loop_i, 2));
+    TRY(dalloc(h, &h->loop_nr, (size_t)LOOP_MAX));
+  }
+  TRY(cudaMemsetAsync(h->loop_i, 0, 2 * sizeof(int), h->st));
+  const bool engine = source == SYMNMF_SRC_LAI && h->o.lai_mode != 1 && chunk <= OBJ_RING;
+  // the device loop needs whole chunks and is recorded once a call repeats
+  // the previous call's parameters; otherwise (and for the other sweep
+  // kernels) the host checks after each chunk
+  auto& L = h->loop;
+  const bool repeat = L.prev_check == check && L.prev_chunk == chunk && L.prev_max_checks == max_checks &&
+                      L.prev_l == h->l && L.prev_target == target;
+  L.prev_check = check;
+  L.prev_chunk = chunk;
+  L.prev_max_checks = max_checks;
+  L.prev_l = h->l;
+  L.prev_target = target;
+  const bool device_loop = engine && max_sweeps % chunk == 0 && max_checks > 1 && repeat;
+  int checks = 0;
+  if (device_loop) {
+    // first pass eagerly: the engine's prologue, and every workspace sized
+    TRYS(lai_engine_sweeps(h, chunk, nullptr));
+    TRYS(residual_dev(h, check));
+    loop_decide_kernel<<<1, 32, 0, h->st>>>(h->scal + S_OBJ, normx_for(h, check), target, max_checks, h->loop_i,
+                                            h->loop_nr, 0, 0);
+    count_launches(1);
+    TRY(cudaGetLastError());
+    TRYS(get_loop_graph(h, check, chunk, target, max_checks));
+    TRY(cudaGraphLaunch(L.exec, h->st));
+    int li[2] = {0, 0};
+    TRY(cudaMemcpyAsync(li, h->loop_i, sizeof(li), cudaMemcpyDeviceToHost, h->st));
+    TRYS(check_device_error(h));
+    checks = li[0];
+    count_launches(1 + (uint64_t)(checks - 1) * L.nkernels);
+  } else {
+    int done = 0;
+    while (done < max_sweeps) {
+      const int m = (max_sweeps - done) < chunk ? (max_sweeps - done) : chunk;
+      TRYS(symnmf_hals_sweep(h, m, source, SYMNMF_RULE_HALS, nullptr));
+      done += m;
+      if (!h->grams_fresh) TRYS(refresh_grams(h));
+      TRYS(residual_dev(h, check));
+      loop_decide_kernel<<<1, 32, 0, h->st>>>(h->scal + S_OBJ, normx_for(h, check), target, max_checks,
+                                              h->loop_i, h->loop_nr, 0, 0);
+      count_launches(1);
+      int li[2] = {0, 0};
+      TRY(cudaMemcpyAsync(li, h->loop_i, sizeof(li), cudaMemcpyDeviceToHost, h->st));
+      TRYS(check_device_error(h));
+      checks = li[0];
+      if (!li[1]) break;
+    }
+  }
+  if (checks < 1 || checks > max_checks) return fail(h, SYMNMF_ECUDA, "residual check loop count");
+  double nr = 0.0;
+  TRY(cudaMemcpy(&nr, h->loop_nr + (checks - 1), sizeof(double), cudaMemcpyDeviceToHost));
+  if (sweeps_out) *sweeps_out = checks * chunk < max_sweeps ? checks * chunk : max_sweeps;
+  if (checks_out) *checks_out = checks;
+  if (nr_out) *nr_out = nr;
   return SYMNMF_OK;
 }
 

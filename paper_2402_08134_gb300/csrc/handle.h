@@ -34,6 +34,7 @@ enum {
   S_COUNT = 40
 };
 constexpr int OBJ_RING = 4096;
+constexpr int LOOP_MAX = 1024;  // residual checks one symnmf_sweep_to_target call records
 
 symnmf_status to_status(cudaError_t e);
 
@@ -109,6 +110,24 @@ struct symnmf_ctx {
   int eng_lai_version = -1;
   bool grams_fresh = false;  // Gd / Gf hold H^T H and W^T W of the current factors
   cudaStream_t cap_st = nullptr;
+
+  // the device-side check loop of symnmf_sweep_to_target: one graph (a WHILE
+  // node around chunk, check and decision), keyed by its parameters and by the
+  // buffers it was recorded with
+  struct Loop {
+    cudaGraphExec_t exec = nullptr;
+    int check = -1, chunk = 0, max_checks = 0, l = 0;
+    double target = 0.0;
+    const void* bufs[5] = {};
+    uint64_t nkernels = 0;  // kernels per body pass
+    // parameters of the previous call: a loop is recorded only when a call
+    // repeats them (recording costs more than the host round trips it saves
+    // in one solve)
+    int prev_check = -1, prev_chunk = 0, prev_max_checks = 0, prev_l = 0;
+    double prev_target = 0.0;
+  } loop;
+  int* loop_i = nullptr;        // [0] checks made, [1] continue flag
+  double* loop_nr = nullptr;    // normalized residual of each check (LOOP_MAX)
 
   // live timing of the tensor-core product kernel (eager calls only)
   bool profiling = false;

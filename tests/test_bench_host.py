@@ -92,6 +92,21 @@ class _FakeSolver:
         self.log.append(("check", src))
         return self.nr, 0.0
 
+    def sweep_to_target(self, target, *, source, check, chunk, max_sweeps):
+        # the contract of symnmf_sweep_to_target: chunks of `chunk` (the last one cut to max_sweeps),
+        # a check after each, stop after the first check at or below the target
+        done = checks = 0
+        nr = float("inf")
+        while done < max_sweeps:
+            m = min(chunk, max_sweeps - done)
+            self.sweep(m, source, False)
+            done += m
+            nr = self.residual(check)[0]
+            checks += 1
+            if nr <= target:
+                break
+        return {"sweeps": done, "checks": checks, "nr": nr}
+
 
 def test_solve_to_target_stops_at_the_first_check_below_target():
     sys.path.insert(0, ROOT)

@@ -212,3 +212,80 @@ def test_paper_schedule_matches_oracle(S):
     s.set_factors(t32(Hi))
     comp = s.solve(method=S.SRC_COMP, l=l, q_max=8, max_iters=300, max_refine=300)
     assert comp["nr_final"] <= full["nr_final"] + 1e-2
+
+
+@pytest.mark.parametrize("xfmt", ["bf16", "f32"])
+def test_sweep_to_target_stops_where_host_checks_stop(S, xfmt):
+    # symnmf_sweep_to_target decides on the device (LAI engine: one graph with a WHILE node); it must
+    # stop at the same check, with the same residual and factors, as sweeps and checks issued one by
+    # one from the host (same kernels in the same order: equal to the last bit)
+    n, k, l, q = 3000, 6, 22, 2
+    X, _ = _gmm_kernel(n, 10, 6, seed=4)
+    Xt = t32(X) if xfmt == "f32" else t32(X).to(torch.bfloat16)
+    Om = gaussian_sketch(n, l, seed=5)
+    Hi = uniform_factor(n, k, seed=6) * O.init_scale(X, k)
+
+    def fresh():
+        s = S.Solver(Xt, k, max_width=l)
+        s.lai_sketch(l, q, t32(Om))
+        s.set_factors(t32(Hi))
+        return s
+
+    a = fresh()
+    nrs = []
+    for _ in range(14):
+        a.sweep(10, source=S.SRC_LAI, record=False)
+        nrs.append(a.residual(S.SRC_X)[0])
+    assert all(np.isfinite(nrs))
+    # the first check at or below the target is check 7 (index 6)
+    stop = 6
+    target = nrs[stop]
+    assert min(nrs[:stop]) > target
+    b = fresh()
+    r = b.sweep_to_target(target, chunk=10, max_sweeps=200)
+    assert (r["checks"], r["sweeps"]) == (stop + 1, 10 * (stop + 1))
+    assert r["nr"] == nrs[stop]
+    c = fresh()
+    for _ in range(stop + 1):
+        c.sweep(10, source=S.SRC_LAI, record=False)
+    for got, ref in zip(b.factors(), c.factors()):
+        assert torch.equal(got, ref)
+    # a target never reached: every allowed check, the last one's residual
+    d = fresh()
+    r = d.sweep_to_target(0.0, chunk=10, max_sweeps=50)
+    assert (r["checks"], r["sweeps"], r["nr"]) == (5, 50, nrs[4])
+    # reached at the first check (no graph launch)
+    e = fresh()
+    r = e.sweep_to_target(1.0, chunk=10, max_sweeps=200)
+    assert (r["checks"], r["sweeps"], r["nr"]) == (1, 10, nrs[0])
+    # the same solve again on the same handle: the repeated call records the device loop (one graph
+    # with a WHILE node), the third replays it
+    for rep in range(2):
+        b.set_factors(t32(Hi))
+        r = b.sweep_to_target(target, chunk=10, max_sweeps=200)
+        assert (r["checks"], r["sweeps"], r["nr"]) == (stop + 1, 10 * (stop + 1), nrs[stop]), rep
+        for got, ref in zip(b.factors(), c.factors()):
+            assert torch.equal(got, ref)
+    # a device loop that continues from the previous call's state and uses all its checks
+    b.sweep_to_target(0.0, chunk=10, max_sweeps=30)
+    r = b.sweep_to_target(0.0, chunk=10, max_sweeps=30)
+    assert (r["checks"], r["sweeps"], r["nr"]) == (3, 30, nrs[stop + 6])
+
+
+def test_sweep_to_target_host_checked_sources(S):
+    # full-X sweeps are checked on the host after each chunk; a ragged last chunk is cut to max_sweeps
+    n, k = 2000, 5
+    X, _ = _gmm_kernel(n, 8, 5, seed=9)
+    Hi = uniform_factor(n, k, seed=10) * O.init_scale(X, k)
+    a = S.Solver(t32(X), k)
+    a.set_factors(t32(Hi))
+    nrs = []
+    for m in (7, 7, 6):
+        a.sweep(m, source=S.SRC_X, record=False)
+        nrs.append(a.residual(S.SRC_X)[0])
+    b = S.Solver(t32(X), k)
+    b.set_factors(t32(Hi))
+    r = b.sweep_to_target(0.0, source=S.SRC_X, check=S.SRC_X, chunk=7, max_sweeps=20)
+    assert (r["checks"], r["sweeps"], r["nr"]) == (3, 20, nrs[2])
+    with pytest.raises(S.SymNMFError):
+        b.sweep_to_target(0.0, source=S.SRC_LAI, chunk=10, max_sweeps=20)  # no sketch yet
