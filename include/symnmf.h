@@ -109,7 +109,8 @@ typedef struct {
 
 typedef struct {
   int32_t gemm;       /* SYMNMF_GEMM_* */
-  int32_t use_graph;  /* 1: record sweep bodies as CUDA graphs once and replay them */
+  int32_t use_graph;  /* 1: record sweep bodies (and the check loop of symnmf_sweep_to_target) as CUDA
+                        graphs once and replay them; 0: launch every kernel from the host */
   int32_t max_width;  /* largest sketch width l to be requested (0: 2k + 10); values
                          above 96 are lowered to 96 */
   int32_t max_samples;/* largest sample count s for LvS calls (0: n) */
@@ -298,7 +299,7 @@ symnmf_status symnmf_residual(symnmf_t h, int source, double* norm_resid, double
  * `target`, or after max_sweeps sweeps.  The residual-check schedule of the
  * experiments (a check every few iterations, stop once the residual is
  * reached), with the decision taken on the device: for SRC_LAI sweeps of the
- * persistent engine with max_sweeps a multiple of chunk, once a call repeats
+ * persistent engine with max_sweeps a multiple of chunk and use_graph set, once a call repeats
  * the previous call's check, chunk, max_sweeps / chunk, target and sketch
  * width, the first chunk and check run eagerly and the rest in one CUDA graph
  * (recorded on that call, replayed by later ones) whose WHILE node repeats

@@ -1331,7 +1331,7 @@ extern "C" symnmf_status symnmf_sweep_to_target(symnmf_t h, int source, int chec
   L.prev_max_checks = max_checks;
   L.prev_l = h->l;
   L.prev_target = target;
-  const bool device_loop = engine && max_sweeps % chunk == 0 && max_checks > 1 && repeat;
+  const bool device_loop = engine && h->o.use_graph && max_sweeps % chunk == 0 && max_checks > 1 && repeat;
   int checks = 0;
   if (device_loop) {
     // first pass eagerly: the engine's prologue, and every workspace sized
