@@ -763,17 +763,6 @@ static symnmf_status get_graph(symnmf_t h, int src, int rule, symnmf_ctx::Graph*
   return SYMNMF_OK;
 }
 
-// The handle's Grams follow the engine's final factors.
-static symnmf_status engine_grams(symnmf_t h) {
-  const int k = h->k;
-  TRY(cudaMemcpyAsync(h->Gd[0], h->eng_G, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
-  TRY(cudaMemcpyAsync(h->Gd[1], h->eng_G + k * k, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
-  TRY(to_float_scaled(h->Gd[0], k, k, nullptr, h->Gf[0], h->st));
-  TRY(to_float_scaled(h->Gd[1], k, k, nullptr, h->Gf[1], h->st));
-  h->grams_fresh = true;
-  return SYMNMF_OK;
-}
-
 // LAI-HALS sweeps in one cooperative launch per chunk of sweeps.
 static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host) {
   const int k = h->k;
@@ -798,7 +787,8 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
       h->eprof_used++;
     }
     TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
-                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, e0, e1, resume));
+                   h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, e0, e1, resume, h->Gd[0],
+                   h->Gd[1], h->Gf[0], h->Gf[1]));
     h->eng_resume_ok = true;
     h->eng_fac_version = h->fac_version;
     h->eng_lai_version = h->lai_version;
@@ -810,7 +800,7 @@ static symnmf_status lai_engine_sweeps(symnmf_t h, int nsweeps, double* obj_host
     }
     done += chunk;
   }
-  if (nsweeps > 0) TRYS(engine_grams(h));
+  if (nsweeps > 0) h->grams_fresh = true;  // the engine wrote the handle's Grams of its final factors
   return SYMNMF_OK;
 }
 
@@ -1224,8 +1214,8 @@ __global__ void loop_seed_kernel(const int* li, cudaGraphConditionalHandle cond)
 static symnmf_status loop_body(symnmf_t h, int check, int chunk, double target, int max_checks,
                                cudaGraphConditionalHandle cond) {
   TRY(lai_engine(h->U, h->lam, h->W, h->H, h->n, h->k, h->l, chunk, h->alpha, h->scal + S_LAI_NORM2, h->eng_ws,
-                 h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, nullptr, nullptr, true));
-  TRYS(engine_grams(h));
+                 h->obj_ring, OBJ_RING, h->eng_G, h->err, h->o.lai_mode != 2, h->st, nullptr, nullptr, true,
+                 h->Gd[0], h->Gd[1], h->Gf[0], h->Gf[1]));
   TRYS(residual_dev(h, check));
   loop_decide_kernel<<<1, 32, 0, h->st>>>(h->scal + S_OBJ, normx_for(h, check), target, max_checks, h->loop_i,
                                           h->loop_nr, cond, 1);

@@ -165,10 +165,14 @@ cudaError_t hybrid_sample(SampleBufs& b, int64_t n, int k, double tau, int s, ui
 // workspace left them, so its saved state replaces the prologue.
 size_t lai_engine_ws_bytes(int l, int k, int obj_cap);
 // ev_begin / ev_end (optional) are recorded right around the kernel launch.
+// Gd_h, Gd_w, Gf_h, Gf_w (optional, all or none): the final H^T H and W^T W
+// also written there, in FP64 and rounded to FP32.
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
                        double* Gout, unsigned* err, bool allow_resident, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, bool resume = false);
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, bool resume = false,
+                       double* Gd_h = nullptr, double* Gd_w = nullptr, float* Gf_h = nullptr,
+                       float* Gf_w = nullptr);
 // Algorithmic FLOPs of one engine launch: per half sweep n (l k [Y = U M] +
 // k^2 [column updates] + l k [U^T F] + k (k + 1) / 2 [F^T F]) FMAs, plus the
 // prologue's n (l k + k (k + 1) / 2) (not run by a resumed launch); two FLOPs per FMA.

@@ -20,7 +20,7 @@ double lai_engine_flops(int64_t n, int k, int l, int nsweeps, bool prologue) {
 cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, int64_t n, int k, int l,
                        int nsweeps, double alpha, const double* normX2, void* ws, double* obj, int obj_cap,
                        double* Gout, unsigned* err, bool allow_resident, cudaStream_t st, cudaEvent_t ev0,
-                       cudaEvent_t ev1, bool resume) {
+                       cudaEvent_t ev1, bool resume, double* Gd_h, double* Gd_w, float* Gf_h, float* Gf_w) {
   if (k < 1 || k > 64 || l < 1 || l > 96 || n < 1 || nsweeps > obj_cap) return cudaErrorInvalidValue;
   char* b = static_cast<char*>(ws);
   const size_t grid = (size_t)num_sms();
@@ -35,7 +35,9 @@ cudaError_t lai_engine(const float* U, const double* lam, float* W, float* H, in
   float* state = reinterpret_cast<float*>(b);
   const int gp = le_gp(k);
   LaiArgs a{U,    lam,   W,    H,   n,       k,    l,   nsweeps, (float)alpha, alpha, normX2, part,
-            fin,  state, objp, obj, obj_cap, Gout, bar, err,     256,          gp,    0,     resume ? 1 : 0};
+            fin,  state, objp, obj, obj_cap, Gout, bar, err,     256,          gp,    0,     resume ? 1 : 0,
+            Gd_h, Gd_w,  Gf_h, Gf_w};
+  if (!Gd_h || !Gd_w || !Gf_h || !Gf_w) a.Gd_h = a.Gd_w = nullptr, a.Gf_h = a.Gf_w = nullptr;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   // the state's pad entries are never written by the kernel (a resumed launch

@@ -83,6 +83,12 @@ struct LaiArgs {
   int gp;                // G held as gp x gp (gp = KMAX of the kernel), zero padded
   int pitch;             // resident: column pitch (RP padded to 8)
   int resume;            // 1: the H-side state saved by the previous launch is current (no prologue)
+  // optional copies of the final Grams for the caller (nullptr: none): H^T H and W^T W in FP64
+  // and rounded to FP32
+  double* Gd_h;
+  double* Gd_w;
+  float* Gf_h;
+  float* Gf_w;
 };
 
 // Final sums: l*k entries of U^T F, k*k of F^T F, then tr, dd.
@@ -577,8 +583,15 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_resident_kernel(LaiArgs a) 
   // Grams after the last sweep for the handle's state: [0] = H^T H, [1] = W^T W
   if (blockIdx.x == 0)
     for (int e = tid; e < k * k; e += LE_THREADS) {
-      a.Gout[e] = __ldcg(a.fin + E + l * k + e);
-      a.Gout[k * k + e] = __ldcg(a.fin + l * k + e);
+      const double gh = __ldcg(a.fin + E + l * k + e), gw = __ldcg(a.fin + l * k + e);
+      a.Gout[e] = gh;
+      a.Gout[k * k + e] = gw;
+      if (a.Gd_h) {
+        a.Gd_h[e] = gh;
+        a.Gd_w[e] = gw;
+        a.Gf_h[e] = (float)gh;
+        a.Gf_w[e] = (float)gw;
+      }
     }
   le_objective_sums(a, shd);
 }
@@ -751,8 +764,15 @@ __global__ void __launch_bounds__(LE_THREADS, 1) lai_streamed_kernel(LaiArgs a) 
   // Grams after the last sweep for the handle's state: [0] = H^T H, [1] = W^T W
   if (blockIdx.x == 0)
     for (int e = tid; e < k * k; e += LE_THREADS) {
-      a.Gout[e] = __ldcg(a.fin + E + l * k + e);
-      a.Gout[k * k + e] = __ldcg(a.fin + l * k + e);
+      const double gh = __ldcg(a.fin + E + l * k + e), gw = __ldcg(a.fin + l * k + e);
+      a.Gout[e] = gh;
+      a.Gout[k * k + e] = gw;
+      if (a.Gd_h) {
+        a.Gd_h[e] = gh;
+        a.Gd_w[e] = gw;
+        a.Gf_h[e] = (float)gh;
+        a.Gf_w[e] = (float)gw;
+      }
     }
   le_objective_sums(a, shd);
 }

@@ -79,26 +79,61 @@ cudaError_t chol_inverse(const double* G, int k, double shift, double drop_tol, 
 // ||T - V Lambda V^T||_F <= 8 l eps32 ||T||_F (about 2e-5 for l = 50), and the
 // eigenvectors are orthonormal to ~1e-7, far below the precision of the
 // products that formed T.
+//
+// One barrier per round: A is double-buffered (a round reads one buffer and
+// writes the other), every thread forms the rotations of the pairs its blocks
+// need from the round's input, and the pairs of every round are tabulated
+// once at the start (they do not depend on A).
+
+// The Schur rotation (c, s) of pair (p, q) of A (p = -1: the pair holds the
+// dummy index, no rotation).
+__device__ __forceinline__ void jac_rotation(const float* A, int l, int p, int q, float& c, float& sn) {
+  c = 1.f;
+  sn = 0.f;
+  if (p < 0) return;
+  const float apq = A[p * l + q];
+  if (apq != 0.f) {
+    const float tau = (A[q * l + q] - A[p * l + p]) / (2.f * apq);
+    const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    c = rsqrtf(1.f + tt * tt);
+    sn = tt * c;
+  }
+}
+
 __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* lam) {
   extern __shared__ float smf[];
   const int L = (l + 1) & ~1;  // padded to even; index l is a dummy when l is odd
   const int m = L / 2;         // disjoint pairs per round
-  float* A = smf;              // l*l
-  float* V = A + l * l;        // l*l
-  float* cs = V + l * l;       // 2 m
-  int* pp = (int*)(cs + L);    // m
-  int* qq = pp + m;            // m
+  // smf: two l*l buffers of A (a round's input and output), then V (l*l)
+  float* V = smf + 2 * l * l;
+  short2* pq = reinterpret_cast<short2*>(V + l * l);  // (L - 1) rounds x m pairs: (p, q), p = -1 for the dummy
   __shared__ double off, tot;
   __shared__ double shr[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < l * l; e += nt) {
     const int i = e / l, j = e - i * l;
-    A[e] = (float)(0.5 * (Ain[i * l + j] + Ain[j * l + i]));
+    smf[e] = (float)(0.5 * (Ain[i * l + j] + Ain[j * l + i]));
     V[e] = (i == j) ? 1.f : 0.f;
   }
+  // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate; a pair with
+  // the dummy index keeps its real index q = l-1.. unrotated (p = -1)
+  for (int e = tid; e < (L - 1) * m; e += nt) {
+    const int round = e / m, i = e - round * m;
+    const int a = (i == 0) ? 0 : ((i - 1 + round) % (L - 1)) + 1;
+    const int bslot = L - 1 - i;
+    const int b = ((bslot - 1 + round) % (L - 1)) + 1;
+    int p = min(a, b), q = max(a, b);
+    if (q >= l) {
+      q = p;  // the only real index of the pair
+      p = -1;
+    }
+    pq[e] = make_short2((short)p, (short)q);
+  }
   __syncthreads();
+  int cur = 0;
   const double lim = 8.0 * l * 5.9604644775390625e-8;  // 8 l 2^-24
   for (int sweep = 0; sweep < 30; ++sweep) {
+    const float* A = smf + cur * l * l;
     double o = 0.0, t = 0.0;
     for (int e = tid; e < l * l; e += nt) {
       const double v = (double)A[e] * (double)A[e];
@@ -114,64 +149,48 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
     __syncthreads();
     if (off <= lim * lim * tot || off == 0.0) break;
     for (int round = 0; round < L - 1; ++round) {
-      // pairs of the circle method: slot 0 fixed, slots 1..L-1 rotate; a pair
-      // with the dummy index keeps its real index q = l-1.. unrotated (p = -1)
-      for (int i = tid; i < m; i += nt) {
-        const int a = (i == 0) ? 0 : ((i - 1 + round) % (L - 1)) + 1;
-        const int bslot = L - 1 - i;
-        const int b = ((bslot - 1 + round) % (L - 1)) + 1;
-        int p = min(a, b), q = max(a, b);
-        float c = 1.f, sn = 0.f;
-        if (q < l) {
-          const float apq = A[p * l + q];
-          if (apq != 0.f) {
-            const float tau = (A[q * l + q] - A[p * l + p]) / (2.f * apq);
-            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + tt * tt);
-            sn = tt * c;
-          }
-        } else {
-          q = p;  // the only real index of the pair
-          p = -1;
-        }
-        pp[i] = p;
-        qq[i] = q;
-        cs[2 * i] = c;
-        cs[2 * i + 1] = sn;
-      }
-      __syncthreads();
-      // A <- J^T A J on every 2x2 block (rows of pair u, columns of pair v) at
-      // once, and V <- V J (rows i, columns of pair v)
+      const float* Ai = smf + cur * l * l;
+      float* Ao = smf + (cur ^ 1) * l * l;
+      const short2* pr = pq + round * m;
+      // Ao <- J^T Ai J on every 2x2 block (rows of pair u, columns of pair v)
+      // at once, and V <- V J (rows i, columns of pair v)
       for (int e = tid; e < m * m + l * m; e += nt) {
         if (e < m * m) {
           const int u = e / m, v = e - u * m;
-          const int pu = pp[u], qu = qq[u], pv = pp[v], qv = qq[v];
-          const float cu = cs[2 * u], su = cs[2 * u + 1], cv = cs[2 * v], sv = cs[2 * v + 1];
+          const short2 su2 = pr[u], sv2 = pr[v];
+          const int pu = su2.x, qu = su2.y, pv = sv2.x, qv = sv2.y;
+          float cu, su, cv, sv;
+          jac_rotation(Ai, l, pu, qu, cu, su);
+          jac_rotation(Ai, l, pv, qv, cv, sv);
           // rows pu (may be -1), qu; columns pv (may be -1), qv
-          const float x = (pu >= 0 && pv >= 0) ? A[pu * l + pv] : 0.f;
-          const float y = (pu >= 0) ? A[pu * l + qv] : 0.f;
-          const float z = (pv >= 0) ? A[qu * l + pv] : 0.f;
-          const float w = A[qu * l + qv];
+          const float x = (pu >= 0 && pv >= 0) ? Ai[pu * l + pv] : 0.f;
+          const float y = (pu >= 0) ? Ai[pu * l + qv] : 0.f;
+          const float z = (pv >= 0) ? Ai[qu * l + pv] : 0.f;
+          const float w = Ai[qu * l + qv];
           const float x1 = cu * x - su * z, z1 = su * x + cu * z;
           const float y1 = cu * y - su * w, w1 = su * y + cu * w;
-          if (pu >= 0 && pv >= 0) A[pu * l + pv] = cv * x1 - sv * y1;
-          if (pu >= 0) A[pu * l + qv] = sv * x1 + cv * y1;
-          if (pv >= 0) A[qu * l + pv] = cv * z1 - sv * w1;
-          A[qu * l + qv] = sv * z1 + cv * w1;
+          if (pu >= 0 && pv >= 0) Ao[pu * l + pv] = cv * x1 - sv * y1;
+          if (pu >= 0) Ao[pu * l + qv] = sv * x1 + cv * y1;
+          if (pv >= 0) Ao[qu * l + pv] = cv * z1 - sv * w1;
+          Ao[qu * l + qv] = sv * z1 + cv * w1;
         } else {
           const int f = e - m * m, row = f / m, v = f - row * m;
-          const int pv = pp[v], qv = qq[v];
+          const short2 sv2 = pr[v];
+          const int pv = sv2.x, qv = sv2.y;
           if (pv >= 0) {
-            const float cv = cs[2 * v], sv = cs[2 * v + 1];
+            float cv, sv;
+            jac_rotation(Ai, l, pv, qv, cv, sv);
             const float a0 = V[row * l + pv], a1 = V[row * l + qv];
             V[row * l + pv] = cv * a0 - sv * a1;
             V[row * l + qv] = sv * a0 + cv * a1;
           }
         }
       }
+      cur ^= 1;
       __syncthreads();
     }
   }
+  const float* A = smf + cur * l * l;
   for (int e = tid; e < l * l; e += nt) Vout[e] = (double)V[e];
   for (int i = tid; i < l; i += nt) lam[i] = (double)A[i * l + i];
 }
@@ -179,7 +198,8 @@ __global__ void jacobi_kernel(const double* Ain, int l, double* Vout, double* la
 cudaError_t jacobi_evd(const double* A, int l, double* V, double* lam, cudaStream_t st) {
   if (l < 1 || l > 96) return cudaErrorInvalidValue;
   const int L = (l + 1) & ~1;
-  const size_t smem = (size_t)2 * l * l * 4 + (size_t)L * 4 + (size_t)L * 4 + 16;
+  // two buffers of A, V, and the (p, q) table of all L - 1 rounds
+  const size_t smem = (size_t)3 * l * l * 4 + (size_t)(L - 1) * (L / 2) * sizeof(short2) + 16;
   cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
