@@ -37,12 +37,16 @@ constexpr int hals_gstride() {
 // T[c HALS_CS + t], tile rows wrow .. wrow + 31), zero padded past n and k.
 // The lanes walk the rows' contiguous span, so each global load instruction
 // covers whole cache lines (one row per thread would touch 32 lines per load).
+// At 64 columns the 16-byte form is unrolled whole, so that all of a lane's
+// loads are issued before its shared-memory stores: the DRAM latency is
+// waited out once per tile, not once per few loads.
 template <int KMAX, bool VEC>
 __device__ __forceinline__ void hals_stage_in(const float* __restrict__ src, int64_t ld, int64_t r0, int64_t n,
                                               int k, float* T, int wrow, int lane) {
   if constexpr (VEC) {
     constexpr int Q = KMAX / 4;
-#pragma unroll 4
+    constexpr int U1 = KMAX == 64 ? 16 : 4;
+#pragma unroll U1
     for (int e = lane; e < 32 * Q; e += 32) {
       const int rr = e / Q, c4 = e - rr * Q;
       const int64_t r = r0 + rr;
@@ -57,6 +61,32 @@ __device__ __forceinline__ void hals_stage_in(const float* __restrict__ src, int
       const int rr = e / KMAX, c = e - rr * KMAX;
       const int64_t r = r0 + rr;
       T[c * HALS_CS + wrow + rr] = (r < n && c < k) ? __ldg(src + r * ld + c) : 0.f;
+    }
+  }
+}
+
+// The 16-byte hals_stage_in of two matrices at once (the rows of Y and of
+// F_fix): twice the loads in flight per round.
+template <int KMAX>
+__device__ __forceinline__ void hals_stage_in2(const float* __restrict__ sa, int64_t lda, float* Ta,
+                                               const float* __restrict__ sb, int64_t ldb, float* Tb, int64_t r0,
+                                               int64_t n, int k, int wrow, int lane) {
+  {
+    constexpr int Q = KMAX / 4;
+    constexpr int U2 = KMAX == 64 ? 8 : 4;  // registers: the row of F_upd is live here
+#pragma unroll U2
+    for (int e = lane; e < 32 * Q; e += 32) {
+      const int rr = e / Q, c4 = e - rr * Q;
+      const int64_t r = r0 + rr;
+      float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+      if (r < n && 4 * c4 < k) {
+        va = __ldg(reinterpret_cast<const float4*>(sa + r * lda) + c4);
+        vb = __ldg(reinterpret_cast<const float4*>(sb + r * ldb) + c4);
+      }
+      float* ta = Ta + 4 * c4 * HALS_CS + wrow + rr;
+      float* tb = Tb + 4 * c4 * HALS_CS + wrow + rr;
+      ta[0] = va.x, ta[HALS_CS] = va.y, ta[2 * HALS_CS] = va.z, ta[3 * HALS_CS] = va.w;
+      tb[0] = vb.x, tb[HALS_CS] = vb.y, tb[2 * HALS_CS] = vb.z, tb[3 * HALS_CS] = vb.w;
     }
   }
 }
@@ -164,10 +194,12 @@ __global__ void __launch_bounds__(HALS_THREADS) hals_kernel(
       }
 #pragma unroll
       for (int c = 0; c < KMAX; ++c) ya[c * HALS_CS] = y[c];
+    } else if constexpr (VEC) {
+      hals_stage_in2<KMAX>(Y, ldy, Ta, Ff, k, Tb, r0, n, k, wrow, lane);
     } else {
-      hals_stage_in<KMAX, VEC>(Y, ldy, r0, n, k, Ta, wrow, lane);
+      hals_stage_in<KMAX, false>(Y, ldy, r0, n, k, Ta, wrow, lane);
     }
-    hals_stage_in<KMAX, VEC>(Ff, k, r0, n, k, Tb, wrow, lane);
+    if (U || !VEC) hals_stage_in<KMAX, VEC>(Ff, k, r0, n, k, Tb, wrow, lane);
     __syncwarp();
     if constexpr (ROT)
       bad |= hals_row_rotating<KMAX, 16>(
