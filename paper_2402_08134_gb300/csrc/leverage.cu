@@ -38,7 +38,10 @@ __global__ void __launch_bounds__(LEV_THREADS) leverage_kernel(const float* __re
     __syncwarp();  // the previous pass's reads of the tile are done
     if constexpr (VEC) {
       constexpr int Q = KMAX / 4;
-#pragma unroll 4
+      // at 64 columns 16 loads per lane in flight per round (the z registers
+      // are not live yet)
+      constexpr int U = KMAX == 64 ? 16 : 4;
+#pragma unroll U
       for (int e = lane; e < 64 * Q; e += 32) {
         const int rr = e / Q, c4 = e - rr * Q;
         const int64_t r = r0 + rr;
